@@ -1,0 +1,351 @@
+"""Benchmark: Relay-BP syndromes/s on one GB300, gross code [[144,12,12]], 12 noisy rounds.
+
+Workload: the phenomenological detector model of the gross code (936 detectors x 2736
+faults, 7344 edges), 12 noisy rounds plus one perfect round, i.i.d. faults with
+p = 0.003, 10^5 syndromes per step, Relay with the App. A.3 leg schedule
+(T_1 = 80, T_r = 60, R = 300, gamma_0 = 0.125, gamma ~ U[-0.24, 0.66]) and S = 5
+solutions, float32 messages.  A step decodes the whole batch with one call.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  --impl reference times the CPU oracle (FP64, all
+host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import BB144, gamma_table, pack_bits, phenomenological_dem, sample_faults, \
+    syndromes_of  # noqa: E402
+
+WORKLOAD = "gross [[144,12,12]] phenomenological T=12 + 1 perfect round, 936x2736, p=0.003"
+SHOTS = 100_000
+SEED = 1
+S_SOLUTIONS = 5
+METRIC = "Relay-BP syndromes/s on 1 GB300 (gross code, 12 rds) and % of roofline"
+
+
+def make_inputs(n_shots: int, seed: int, first_shot: int = 0):
+    P = phenomenological_dem(BB144, 12, 0.003)
+    F = sample_faults(P.p, seed, n_shots, first_shot=first_shot)
+    sig = syndromes_of(P.row_ptr, P.col_idx, F)
+    gam = gamma_table(P.N, 300, 0.125, -0.24, 0.66, seed)
+    return P, sig, gam
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"qldpc_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------
+# the reference arm: the CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------------------
+def cpu_oracle_rate(P, sig, gam, target_s: float = 10.0, precision: str = "f64"):
+    from oracle import build as oracle_build
+    from oracle.relay import RelayParams, relay_decode
+    oracle_build.build()
+    prm = RelayParams(stop_after_solutions=S_SOLUTIONS)
+    cores = os.cpu_count() or 1
+    cal = min(2000, sig.shape[0])
+    t0 = time.perf_counter()
+    relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig[:cal], prm, precision=precision,
+                 nthreads=cores)
+    dt = time.perf_counter() - t0
+    n = int(min(sig.shape[0], max(cal, cal * target_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    r = relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig[:n], prm, precision=precision,
+                     nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "syndromes/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of the {sig.shape[0]} syndromes, FP64 oracle, OpenMP over "
+                      f"shots on {cores} host threads, {dt:.1f} s",
+            "edge_updates_per_s": float(P.E * r.iters.sum() / dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    P, sig, gam = make_inputs(SHOTS, SEED)
+    from oracle import build as oracle_build
+    from oracle.relay import RelayParams, relay_decode
+    oracle_build.build()
+    cores = os.cpu_count() or 1
+    prm = RelayParams(stop_after_solutions=S_SOLUTIONS)
+    # a bounded sample per step so that warm-up + steps end within a few minutes
+    per_step = int(os.environ.get("QLDPC_REF_SHOTS", "2000"))
+    times = []
+    off = 0
+    for k in range(args.warmup + args.steps):
+        s = sig[off:off + per_step]
+        off = (off + per_step) % (SHOTS - per_step)
+        t0 = time.perf_counter()
+        relay_decode(P.row_ptr, P.col_idx, P.p, gam, s, prm, precision="f64", nthreads=cores)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "syndromes/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "shots_per_step": per_step, "S": S_SOLUTIONS,
+                       "parallelism": "OpenMP over shots", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{per_step} syndromes per step of the same workload"},
+            "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def timed_decode(dec, syn, out, steps, warmup, stream, flush):
+    """Per-step CUDA-event times (ms) of the decode call, L2 flushed between steps."""
+    import torch
+    for _ in range(warmup):
+        dec.decode(syn, out=out, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        dec.decode(syn, out=out, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_21660_gb300 import (QLDPC_KERNEL_BASELINE, QLDPC_KERNEL_FUSED,
+                                        QLDPC_MSG_FP16, QLDPC_MSG_FP32, RelayConfig, RelayDecoder)
+    from paper_2511_21660_gb300 import qldpc as Q
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # weak scaling: each rank decodes its own 10^5 shots (shard `rank` of the shot stream)
+    P, sig, gam = make_inputs(SHOTS, SEED)
+    if rank > 0:
+        F = sample_faults(P.p, SEED, SHOTS, first_shot=rank * SHOTS)
+        sig = syndromes_of(P.row_ptr, P.col_idx, F)
+    packed = pack_bits(sig)
+    syn = torch.from_numpy(packed.view(np.int64)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
+    stream = torch.cuda.Stream(device=dev)
+
+    cfg = RelayConfig(stop_after_solutions=S_SOLUTIONS, msg_precision=QLDPC_MSG_FP32,
+                      kernel=QLDPC_KERNEL_FUSED)
+    dec = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam, cfg, device=local)
+    out = dec.outputs(SHOTS)
+
+    # the headline measurement
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        times = timed_decode(dec, syn, out, args.steps, args.warmup, stream, flush)
+        t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    ms = sum(times) / len(times)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    iters = out[3].cpu().numpy().astype(np.int64)
+    conv = out[2].cpu().numpy()
+    total_iters = int(iters.sum())
+    value = ws * SHOTS / (ms / 1e3)
+
+    if rank != 0:
+        dec.close()
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the decode kernel: algorithmic shared-memory message traffic, four
+    # message accesses (read nu, write mu, read mu, write nu) per edge per iteration
+    msg_bytes = 4
+    alg_bytes = 4 * msg_bytes * P.E * total_iters
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    sms = dec.info.num_sms
+    peak = 128 * sms * 2070e6 / 1e9      # 128 B/clk/SM of shared memory at the 2070 MHz max clock
+    roofline = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "note": f"algorithmic bytes = 4 x {msg_bytes} B x E x iterations "
+                        f"({alg_bytes / 1e9:.2f} GB per launch); peak derived from "
+                        f"{sms} SMs x 128 B/clk x 2070 MHz"}
+
+    # variants measured in the same run: FP16 messages and the plain baseline kernel
+    variants = {}
+    for name, vcfg in (("fused_fp16", RelayConfig(stop_after_solutions=S_SOLUTIONS,
+                                                  msg_precision=QLDPC_MSG_FP16,
+                                                  kernel=QLDPC_KERNEL_FUSED)),
+                       ("baseline_fp32", RelayConfig(stop_after_solutions=S_SOLUTIONS,
+                                                     msg_precision=QLDPC_MSG_FP32,
+                                                     kernel=QLDPC_KERNEL_BASELINE))):
+        vd = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam, vcfg, device=local)
+        vo = vd.outputs(SHOTS)
+        vt = timed_decode(vd, syn, vo, max(3, min(args.steps, 5)), 3, stream, flush)
+        vms = sum(vt) / len(vt)
+        same = bool(torch.equal(vo[0], out[0]) and torch.equal(vo[3], out[3]))
+        variants[name] = {"value": SHOTS / (vms / 1e3), "unit": "syndromes/s",
+                          "ms_per_step": vms, "block_threads": vd.info.block_threads,
+                          "blocks_per_sm": vd.info.blocks_per_sm,
+                          "identical_to_fp32_fused": same}
+        vd.close()
+    variants["fused_fp32_speedup_vs_baseline"] = (value / ws) / variants["baseline_fp32"]["value"]
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    sw, cw = dec.syndrome_words, dec.correction_words
+    h_syn = torch.from_numpy(packed.view(np.int64)).pin_memory()
+    h_cor = torch.empty((SHOTS, cw), dtype=torch.int64).pin_memory()
+    h_legs = torch.empty(SHOTS, dtype=torch.int32).pin_memory()
+    h_conv = torch.empty(SHOTS, dtype=torch.uint8).pin_memory()
+    h_it = torch.empty(SHOTS, dtype=torch.int32).pin_memory()
+
+    def host_call():
+        Q.qldpc_decode_batch_host(dec.handle, ctypes.c_void_p(h_syn.data_ptr()), SHOTS,
+                                  ctypes.c_void_p(h_cor.data_ptr()),
+                                  ctypes.c_void_p(h_legs.data_ptr()),
+                                  ctypes.c_void_p(h_conv.data_ptr()),
+                                  ctypes.c_void_p(h_it.data_ptr()))
+    for _ in range(max(1, args.warmup)):
+        host_call()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        host_call()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": SHOTS / (sum(e2e_t) / len(e2e_t)), "unit": "syndromes/s",
+           "h2d_bytes_per_step": int(SHOTS * sw * 8),
+           "d2h_bytes_per_step": int(SHOTS * (cw * 8 + 4 + 1 + 4))}
+    assert np.array_equal(h_cor.numpy(), out[0].cpu().numpy()), "host path differs"
+
+    cpu = cpu_oracle_rate(P, sig, gam) if args.cpu_baseline else None
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "syndromes/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shots_per_step": SHOTS, "S": S_SOLUTIONS,
+                   "relay": "T1=80 T2=60 R=300 gamma0=0.125 gamma~U[-0.24,0.66]",
+                   "messages": "float32", "kernel": "fused persistent",
+                   "block_threads": dec.info.block_threads,
+                   "blocks_per_sm": dec.info.blocks_per_sm, "grid": dec.info.grid_blocks,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "flushed between steps (256 MB write)"},
+        "edge_updates_per_s": ws * P.E * total_iters / (ms / 1e3),
+        "iterations_per_shot": {"mean": total_iters / SHOTS, "max": int(iters.max()),
+                                "p99": float(np.percentile(iters, 99))},
+        "converged_fraction": float(conv.mean()),
+        "roofline": roofline, "variants": variants, "e2e": e2e, "cpu_baseline": cpu,
+        "clocks": clocks, "gpu_launches": args.steps,
+        "wall_s_timed_region": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    dec.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * qldpc.h — C ABI of the GB300 batched Relay-BP decoder (libqldpc.so).
+ *
+ * Relay decoding (paper Sec. 2.3, "Relay decoding"; parameters App. A.3) of many
+ * syndromes of one decoding problem (H, p) (paper Sec. 2.1, "Noise and decoding").
+ * For each syndrome sigma the decoder runs legs of disordered-memory min-sum
+ * belief propagation (DMem-BP):
+ *     lambda_j(t) = (1 - gamma_j) lambda_j(0) + gamma_j Lambda_j(t-1)
+ *     mu_{i->j}(t) = (-1)^{sigma_i} prod_{j' in N(i)\j} sign(nu_{j'->i}(t-1)) min |nu_{j'->i}(t-1)|
+ *     nu_{j->i}(t) = lambda_j(t) + sum_{i' in N(j)\i} mu_{i'->j}(t)
+ *     Lambda_j(t) = lambda_j(t) + sum_{i in N(j)} mu_{i->j}(t),  F_j = [Lambda_j < 0]
+ * until H F = sigma (a solution) or T_r iterations; leg r >= 2 is warm-started from
+ * the previous leg's terminal marginals; decoding stops after S solutions or after
+ * the last leg and returns the lowest-weight solution (W = sum_j F_j w_j).
+ *
+ * Conventions for every entry point:
+ *   - Return value: QLDPC_OK (0) or a negative QLDPC_ERR_* code; qldpc_last_error()
+ *     then describes the failure for the calling thread.  Nothing aborts or traps.
+ *   - Bit vectors are packed little-endian into uint64 words: bit k of word w is
+ *     entry 64*w + k.  Padding bits of syndromes are ignored; padding bits of
+ *     corrections are written as zero.
+ *   - A decoder handle may be used by one host thread at a time, and its decode
+ *     calls must not overlap on the GPU (they share the handle's work counter).
+ *   - "device" pointers are CUDA device (or managed) memory of the handle's device;
+ *     "host" pointers are ordinary (preferably pinned) host memory.
+ */
+#ifndef QLDPC_H
+#define QLDPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QLDPC_OK 0
+#define QLDPC_ERR_INVALID_ARG (-1)  /* a pointer, size or value is outside its contract   */
+#define QLDPC_ERR_CUDA (-2)         /* a CUDA runtime call failed                         */
+#define QLDPC_ERR_OOM (-3)          /* a device or host allocation failed                 */
+#define QLDPC_ERR_UNSUPPORTED (-4)  /* the graph exceeds what the kernels are built for   */
+
+/* Message storage precision (variable-node sums are always float32). */
+#define QLDPC_MSG_FP32 0
+#define QLDPC_MSG_FP16 1
+
+/* Kernel selection. */
+#define QLDPC_KERNEL_AUTO 0      /* the fused persistent kernel                          */
+#define QLDPC_KERNEL_BASELINE 1  /* plain one-shot-per-block float32 kernel (reference)  */
+#define QLDPC_KERNEL_FUSED 2     /* fused persistent kernel                              */
+
+/* Relay parameters (paper App. A.3 gives T_1 = 80, T_r = 60, R = 300, S = 1). */
+typedef struct {
+    int32_t legs_after_first;     /* R >= 0: relay legs after the first leg                 */
+    int32_t iters_first;          /* T_1 >= 1: iteration limit of the first leg             */
+    int32_t iters_later;          /* T_r >= 1: iteration limit of legs 2..R+1               */
+    int64_t max_total_iters;      /* iteration budget per shot over all legs; <= 0: none    */
+    int32_t stop_after_solutions; /* S >= 1                                                 */
+    int32_t warm_start_mode;      /* 0: lambda(0) <- previous terminal marginals (paper);
+                                     1: lambda(0) = nu(0) = w, Lambda(0) carried over       */
+    int32_t msg_precision;        /* QLDPC_MSG_FP32 or QLDPC_MSG_FP16                       */
+    int32_t kernel;               /* QLDPC_KERNEL_*                                         */
+    int32_t block_threads;        /* threads per block; 0 = chosen by the library          */
+    float llr_clip;               /* saturation bound C of messages and marginals;
+                                     <= 0: 65504 (FP16 storage) or 1e30 (FP32)              */
+    const float *gamma_table;     /* host, [(R+1)][N] row-major: row r holds the memory
+                                     strengths gamma_j of leg r+1 (row 0 = first leg).
+                                     Copied at create time; finite values required.        */
+} qldpc_relay_params;
+
+typedef struct qldpc_decoder qldpc_decoder; /* opaque */
+
+/* Facts about a created decoder (for tests, tuning and reports). */
+typedef struct {
+    int32_t M, N, E;              /* checks, faults, edges of H                              */
+    int32_t max_check_degree, max_fault_degree;
+    int32_t kernel;               /* QLDPC_KERNEL_BASELINE or QLDPC_KERNEL_FUSED             */
+    int32_t msg_precision;
+    int32_t block_threads;
+    int32_t blocks_per_sm;        /* resident blocks per SM of the chosen kernel             */
+    int32_t num_sms;
+    int32_t grid_blocks;          /* persistent grid size (fused kernel)                     */
+    int32_t smem_bytes;           /* dynamic shared memory per block                         */
+    int32_t syndrome_words;       /* ceil(M/64): uint64 words per syndrome                   */
+    int32_t correction_words;     /* ceil(N/64): uint64 words per correction                 */
+} qldpc_info;
+
+/*
+ * Create a decoder for H (M x N, given as CSR: row_ptr[M+1], col_idx[E], columns
+ * strictly increasing within a row, 0 <= col < N) with fault probabilities
+ * priors[N] in (0, 1) (paper Sec. 2.1) and Relay parameters *prm.  All inputs are
+ * host memory and are copied; the caller may free them on return.  device: CUDA
+ * device ordinal.  *out receives the handle (NULL on failure).
+ * Errors: INVALID_ARG (malformed CSR, prior outside (0,1), bad parameter),
+ * UNSUPPORTED (a check degree above 32, a fault degree above 8, or a graph whose
+ * state does not fit in shared memory), OOM, CUDA.
+ */
+int qldpc_create(qldpc_decoder **out, int32_t M, int32_t N, const int32_t *row_ptr,
+                 const int32_t *col_idx, const double *priors, const qldpc_relay_params *prm,
+                 int device);
+
+/*
+ * Decode B syndromes.  syndromes: device, [B][ceil(M/64)] uint64.  Outputs, all
+ * device: corrections [B][ceil(N/64)] uint64 (the kept solution, or the last
+ * iteration's decision when no solution was found); legs_used [B] int32 (legs run);
+ * converged [B] uint8 (1 iff at least one valid correction was found); iters [B]
+ * int32 (DMem-BP iterations run over all legs).  legs_used, converged and iters may
+ * be NULL.  stream: a cudaStream_t (NULL = legacy default stream).  The call is
+ * asynchronous on stream: it returns after the launch is queued.  B = 0 is a no-op.
+ * Errors: INVALID_ARG (NULL handle, NULL syndromes/corrections with B > 0, B < 0 or
+ * above 2^31-1, a pointer that is not device memory), CUDA (launch failure).
+ */
+int qldpc_decode_batch(qldpc_decoder *d, const uint64_t *syndromes, int64_t B,
+                       uint64_t *corrections, int32_t *legs_used, uint8_t *converged,
+                       int32_t *iters, void *stream);
+
+/*
+ * Same as qldpc_decode_batch with HOST buffers: copies the syndromes to device
+ * buffers owned by the handle (grown on demand), decodes on the handle's internal
+ * stream, copies the results back and waits for completion.  Pinned host memory
+ * gives full copy bandwidth.  legs_used, converged, iters may be NULL.
+ * Errors: as qldpc_decode_batch, plus OOM when the staging buffers cannot grow.
+ */
+int qldpc_decode_batch_host(qldpc_decoder *d, const uint64_t *syndromes, int64_t B,
+                            uint64_t *corrections, int32_t *legs_used, uint8_t *converged,
+                            int32_t *iters);
+
+/*
+ * Run T iterations of the first leg (memory strengths = row 0 of the gamma table)
+ * on B syndromes with no early exit, recording every iteration, for checking
+ * message precision.  Outputs (device, float32, may be NULL):
+ * marginals [T][B][N] = Lambda(t); nu [T][B][E] and mu [T][B][E] = the two message
+ * directions after iteration t, in CSR edge order (edge e = position in col_idx).
+ * Uses the decoder's message precision and kernel family (fused kernel only).
+ * Asynchronous on stream.  Errors: INVALID_ARG, UNSUPPORTED (baseline kernel), CUDA.
+ */
+int qldpc_trace_first_leg(qldpc_decoder *d, const uint64_t *syndromes, int64_t B, int32_t T,
+                          float *marginals, float *nu, float *mu, void *stream);
+
+/* Fill *info.  Errors: INVALID_ARG. */
+int qldpc_get_info(const qldpc_decoder *d, qldpc_info *info);
+
+/* Wait for the handle's work, then free everything it owns.  NULL is ignored. */
+void qldpc_destroy(qldpc_decoder *d);
+
+/* Static description of a status code. */
+const char *qldpc_status_string(int status);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *qldpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLDPC_H */

@@ -1,0 +1,494 @@
+// Host side of the C ABI declared in include/qldpc.h: input validation, graph
+// layout for the kernels, kernel selection, launches and buffer staging.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qldpc.h"
+#include "qldpc_internal.h"
+
+using namespace qldpc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define QL_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            int code_ = e_ == cudaErrorMemoryAllocation ? QLDPC_ERR_OOM : QLDPC_ERR_CUDA; \
+            return fail(code_, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+        }                                                                                \
+    } while (0)
+
+// Makes `dev` current for the scope and restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct qldpc_decoder {
+    int device = 0;
+    int M = 0, N = 0, E = 0, dc_max = 0, dv_max = 0;
+    DevParams prm{};
+    int kernel = QLDPC_KERNEL_FUSED;
+    int msg_fp16 = 0;
+    const FusedKernel *fk = nullptr;        // decode kernel
+    const FusedKernel *fk_trace = nullptr;  // trace kernel
+    size_t trace_smem = 0;
+    int block_threads = 0, blocks_per_sm = 0, num_sms = 0, grid = 0;
+    size_t smem = 0;
+    FusedGraph fg{};
+    BaseGraph bg{};
+    void *arena = nullptr;
+    unsigned int *counter = nullptr;
+    cudaStream_t stream = nullptr;  // internal stream of the host-buffer entry point
+    void *stage = nullptr;
+    int64_t stage_B = 0;
+};
+
+namespace {
+
+int validate_graph(int32_t M, int32_t N, const int32_t *row_ptr, const int32_t *col_idx,
+                   const double *priors) {
+    if (M < 1 || N < 1) return fail(QLDPC_ERR_INVALID_ARG, "need M >= 1 and N >= 1 (got %d, %d)", M, N);
+    if (!row_ptr || !priors) return fail(QLDPC_ERR_INVALID_ARG, "row_ptr and priors must not be NULL");
+    if (row_ptr[0] != 0) return fail(QLDPC_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+    for (int i = 0; i < M; ++i)
+        if (row_ptr[i + 1] < row_ptr[i])
+            return fail(QLDPC_ERR_INVALID_ARG, "row_ptr decreases at row %d", i);
+    const int64_t E = row_ptr[M];
+    if (E > 0 && !col_idx) return fail(QLDPC_ERR_INVALID_ARG, "col_idx must not be NULL");
+    for (int i = 0; i < M; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (col_idx[e] < 0 || col_idx[e] >= N)
+                return fail(QLDPC_ERR_INVALID_ARG, "col_idx[%d] = %d outside [0, %d)", e, col_idx[e], N);
+            if (e > row_ptr[i] && col_idx[e] <= col_idx[e - 1])
+                return fail(QLDPC_ERR_INVALID_ARG, "columns of row %d are not strictly increasing", i);
+        }
+    for (int j = 0; j < N; ++j)
+        if (!(priors[j] > 0.0 && priors[j] < 1.0))
+            return fail(QLDPC_ERR_INVALID_ARG, "prior %d = %g outside (0, 1)", j, priors[j]);
+    return QLDPC_OK;
+}
+
+int validate_params(const qldpc_relay_params *p, int N) {
+    if (!p) return fail(QLDPC_ERR_INVALID_ARG, "params must not be NULL");
+    if (p->legs_after_first < 0) return fail(QLDPC_ERR_INVALID_ARG, "legs_after_first < 0");
+    if (p->iters_first < 1 || p->iters_later < 1)
+        return fail(QLDPC_ERR_INVALID_ARG, "iteration limits must be >= 1");
+    if (p->stop_after_solutions < 1) return fail(QLDPC_ERR_INVALID_ARG, "stop_after_solutions < 1");
+    if (p->warm_start_mode != 0 && p->warm_start_mode != 1)
+        return fail(QLDPC_ERR_INVALID_ARG, "warm_start_mode must be 0 or 1");
+    if (p->msg_precision != QLDPC_MSG_FP32 && p->msg_precision != QLDPC_MSG_FP16)
+        return fail(QLDPC_ERR_INVALID_ARG, "unknown msg_precision %d", p->msg_precision);
+    if (p->kernel < QLDPC_KERNEL_AUTO || p->kernel > QLDPC_KERNEL_FUSED)
+        return fail(QLDPC_ERR_INVALID_ARG, "unknown kernel %d", p->kernel);
+    if (p->block_threads < 0) return fail(QLDPC_ERR_INVALID_ARG, "block_threads < 0");
+    if (!(std::isfinite(p->llr_clip))) return fail(QLDPC_ERR_INVALID_ARG, "llr_clip is not finite");
+    if (p->msg_precision == QLDPC_MSG_FP16 && p->llr_clip > 65504.0f)
+        return fail(QLDPC_ERR_INVALID_ARG, "llr_clip above the binary16 range");
+    if (!p->gamma_table) return fail(QLDPC_ERR_INVALID_ARG, "gamma_table must not be NULL");
+    const size_t n = (size_t)(p->legs_after_first + 1) * N;
+    for (size_t q = 0; q < n; ++q)
+        if (!std::isfinite(p->gamma_table[q]))
+            return fail(QLDPC_ERR_INVALID_ARG, "gamma_table[%zu] is not finite", q);
+    return QLDPC_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Picks the compiled fused-kernel family for the graph's degrees.
+int pick_family(int dc, int dv, int fp16, const FusedKernel **tab, int *n) {
+    if (dc <= 8 && dv <= 4) {
+        if (fp16) fused_table_f16_8_4(tab, n); else fused_table_f32_8_4(tab, n);
+    } else if (dc <= 16 && dv <= 8) {
+        if (fp16) fused_table_f16_16_8(tab, n); else fused_table_f32_16_8(tab, n);
+    } else if (dc <= 32 && dv <= 8) {
+        if (fp16) fused_table_f16_32_8(tab, n); else fused_table_f32_32_8(tab, n);
+    } else {
+        return fail(QLDPC_ERR_UNSUPPORTED,
+                    "check degree %d / fault degree %d above the supported 32 / 8", dc, dv);
+    }
+    return QLDPC_OK;
+}
+
+int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx,
+                const std::vector<float> &w, const float *gamma, int block_threads) {
+    const int M = d->M, N = d->N, E = d->E;
+    const FusedKernel *tab = nullptr;
+    int ntab = 0;
+    int rc = pick_family(d->dc_max, d->dv_max, d->msg_fp16, &tab, &ntab);
+    if (rc) return rc;
+    const int DC = tab[0].dc, DV = tab[0].dv;
+    for (int q = 0; q < ntab && !d->fk; ++q)
+        if ((long long)tab[q].threads * tab[q].vpt >= N &&
+            (block_threads == 0 || tab[q].threads == block_threads))
+            d->fk = &tab[q];
+    if (!d->fk)
+        return fail(QLDPC_ERR_UNSUPPORTED, "no compiled kernel for N = %d with %d threads", N,
+                    block_threads);
+    if ((long long)tab[ntab - 1].threads * tab[ntab - 1].vpt >= N) d->fk_trace = &tab[ntab - 1];
+
+    FusedGraph &g = d->fg;
+    g.M = M;
+    g.N = N;
+    g.E = E;
+    g.Mp = (M + 31) / 32 * 32;
+    g.syn_words = (M + 63) / 64;
+    g.cor_words = (N + 63) / 64;
+    g.f_words = 2 * g.cor_words + 2;
+
+    std::vector<uint8_t> chk_deg(M), var_deg(N, 0);
+    std::vector<int32_t> chk_col((size_t)M * DC, N), var_slot((size_t)N * DV, 0);
+    std::vector<int32_t> slot_edge((size_t)DC * g.Mp, -1);
+    for (int i = 0; i < M; ++i) {
+        chk_deg[i] = (uint8_t)(row_ptr[i + 1] - row_ptr[i]);
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int k = e - row_ptr[i], j = col_idx[e];
+            const int slot = k * g.Mp + i;
+            chk_col[(size_t)i * DC + k] = j;
+            slot_edge[slot] = e;
+            var_slot[(size_t)j * DV + var_deg[j]++] = slot;  // rows ascending => checks ascending
+        }
+    }
+
+    const int msg_bytes = d->msg_fp16 ? 2 : 4;
+    d->smem = fused_smem_bytes(g.Mp, DC, msg_bytes, g.f_words, g.syn_words);
+    int optin = 0;
+    QL_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device));
+    QL_CUDA(cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, d->device));
+    if (d->smem > (size_t)optin)
+        return fail(QLDPC_ERR_UNSUPPORTED, "per-shot state needs %zu B of shared memory, above %d",
+                    d->smem, optin);
+    QL_CUDA(cudaFuncSetAttribute(d->fk->decode_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)d->smem));
+    QL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d->blocks_per_sm, d->fk->decode_fn,
+                                                          d->fk->threads, d->smem));
+    if (d->blocks_per_sm < 1)
+        return fail(QLDPC_ERR_UNSUPPORTED, "the decode kernel cannot be resident on an SM");
+    if (d->fk_trace) {
+        d->trace_smem = d->smem;
+        QL_CUDA(cudaFuncSetAttribute(d->fk_trace->trace_fn,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem));
+    }
+    d->block_threads = d->fk->threads;
+    d->grid = d->num_sms * d->blocks_per_sm;
+
+    // one device arena for every graph array
+    const size_t R1 = (size_t)d->prm.R + 1;
+    size_t off[8], o = 0;
+    const size_t sizes[8] = {(size_t)M, sizeof(int32_t) * M * DC, (size_t)N,
+                             sizeof(int32_t) * N * DV, sizeof(float) * N, sizeof(float) * R1 * N,
+                             sizeof(int32_t) * DC * g.Mp, sizeof(unsigned int) * 4};
+    for (int q = 0; q < 8; ++q) {
+        off[q] = o;
+        o = align_up(o + sizes[q], 256);
+    }
+    QL_CUDA(cudaMalloc(&d->arena, o));
+    char *base = static_cast<char *>(d->arena);
+    const void *src[7] = {chk_deg.data(), chk_col.data(), var_deg.data(), var_slot.data(),
+                          w.data(), gamma, slot_edge.data()};
+    for (int q = 0; q < 7; ++q)
+        QL_CUDA(cudaMemcpy(base + off[q], src[q], sizes[q], cudaMemcpyHostToDevice));
+    g.chk_deg = reinterpret_cast<const uint8_t *>(base + off[0]);
+    g.chk_col = reinterpret_cast<const int32_t *>(base + off[1]);
+    g.var_deg = reinterpret_cast<const uint8_t *>(base + off[2]);
+    g.var_slot = reinterpret_cast<const int32_t *>(base + off[3]);
+    g.w = reinterpret_cast<const float *>(base + off[4]);
+    g.gamma = reinterpret_cast<const float *>(base + off[5]);
+    g.slot_edge = reinterpret_cast<const int32_t *>(base + off[6]);
+    d->counter = reinterpret_cast<unsigned int *>(base + off[7]);
+    QL_CUDA(cudaMemset(d->counter, 0, sizeof(unsigned int) * 4));
+    return QLDPC_OK;
+}
+
+int setup_baseline(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx,
+                   const std::vector<float> &w, const float *gamma) {
+    const int M = d->M, N = d->N, E = d->E;
+    if (d->msg_fp16) return fail(QLDPC_ERR_UNSUPPORTED, "the baseline kernel stores float32 messages");
+    std::vector<int32_t> var_ptr(N + 1, 0), var_edges(std::max(E, 1)), fill(N, 0);
+    for (int e = 0; e < E; ++e) var_ptr[col_idx[e] + 1]++;
+    for (int j = 0; j < N; ++j) var_ptr[j + 1] += var_ptr[j];
+    for (int e = 0; e < E; ++e) {
+        const int j = col_idx[e];
+        var_edges[var_ptr[j] + fill[j]++] = e;
+    }
+    d->smem = baseline_smem_bytes(M, N, E);
+    int optin = 0;
+    QL_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device));
+    QL_CUDA(cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, d->device));
+    if (d->smem > (size_t)optin)
+        return fail(QLDPC_ERR_UNSUPPORTED, "baseline kernel needs %zu B of shared memory, above %d",
+                    d->smem, optin);
+    QL_CUDA(cudaFuncSetAttribute(baseline_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)d->smem));
+    QL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d->blocks_per_sm, baseline_fn(), 256,
+                                                          d->smem));
+    d->block_threads = 256;
+    d->grid = 0;
+    const size_t R1 = (size_t)d->prm.R + 1;
+    size_t off[6], o = 0;
+    const size_t sizes[6] = {sizeof(int32_t) * (M + 1), sizeof(int32_t) * std::max(E, 1),
+                             sizeof(int32_t) * (N + 1), sizeof(int32_t) * std::max(E, 1),
+                             sizeof(float) * N, sizeof(float) * R1 * N};
+    for (int q = 0; q < 6; ++q) {
+        off[q] = o;
+        o = align_up(o + sizes[q], 256);
+    }
+    QL_CUDA(cudaMalloc(&d->arena, o));
+    char *base = static_cast<char *>(d->arena);
+    const void *src[6] = {row_ptr, E > 0 ? (const void *)col_idx : (const void *)var_edges.data(),
+                          var_ptr.data(), var_edges.data(), w.data(), gamma};
+    for (int q = 0; q < 6; ++q)
+        QL_CUDA(cudaMemcpy(base + off[q], src[q], sizes[q], cudaMemcpyHostToDevice));
+    BaseGraph &g = d->bg;
+    g.M = M;
+    g.N = N;
+    g.E = E;
+    g.syn_words = (M + 63) / 64;
+    g.cor_words = (N + 63) / 64;
+    g.row_ptr = reinterpret_cast<const int32_t *>(base + off[0]);
+    g.col_idx = reinterpret_cast<const int32_t *>(base + off[1]);
+    g.var_ptr = reinterpret_cast<const int32_t *>(base + off[2]);
+    g.var_edges = reinterpret_cast<const int32_t *>(base + off[3]);
+    g.w = reinterpret_cast<const float *>(base + off[4]);
+    g.gamma = reinterpret_cast<const float *>(base + off[5]);
+    return QLDPC_OK;
+}
+
+int launch(qldpc_decoder *d, const uint64_t *syn, int64_t B, DecodeOut out, cudaStream_t st) {
+    if (d->kernel == QLDPC_KERNEL_BASELINE) {
+        QL_CUDA(launch_baseline((int)B, d->block_threads, d->smem, st, d->bg, d->prm, syn, out));
+        return QLDPC_OK;
+    }
+    QL_CUDA(cudaMemsetAsync(d->counter, 0, sizeof(unsigned int), st));
+    const int grid = (int)std::min<int64_t>(d->grid, B);
+    QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, syn, (int)B, out,
+                                 d->counter));
+    return QLDPC_OK;
+}
+
+int check_batch(const qldpc_decoder *d, const void *syn, int64_t B, const void *corr) {
+    if (!d) return fail(QLDPC_ERR_INVALID_ARG, "decoder handle is NULL");
+    if (B < 0 || B > 0x7fffffffLL) return fail(QLDPC_ERR_INVALID_ARG, "batch size %lld out of range", (long long)B);
+    if (B > 0 && (!syn || !corr)) return fail(QLDPC_ERR_INVALID_ARG, "syndromes and corrections must not be NULL");
+    return QLDPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qldpc_create(qldpc_decoder **out, int32_t M, int32_t N, const int32_t *row_ptr,
+                 const int32_t *col_idx, const double *priors, const qldpc_relay_params *prm,
+                 int device) {
+    g_last_error.clear();
+    if (!out) return fail(QLDPC_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    int rc = validate_graph(M, N, row_ptr, col_idx, priors);
+    if (rc) return rc;
+    rc = validate_params(prm, N);
+    if (rc) return rc;
+    int ndev = 0;
+    QL_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(QLDPC_ERR_INVALID_ARG, "device %d of %d", device, ndev);
+    DeviceGuard guard(device);
+    QL_CUDA(guard.err);
+
+    qldpc_decoder *d = new (std::nothrow) qldpc_decoder();
+    if (!d) return fail(QLDPC_ERR_OOM, "host allocation failed");
+    d->device = device;
+    d->M = M;
+    d->N = N;
+    d->E = row_ptr[M];
+    std::vector<int> vdeg(N, 0);
+    for (int e = 0; e < d->E; ++e) vdeg[col_idx[e]]++;
+    for (int i = 0; i < M; ++i) d->dc_max = std::max(d->dc_max, row_ptr[i + 1] - row_ptr[i]);
+    for (int j = 0; j < N; ++j) d->dv_max = std::max(d->dv_max, vdeg[j]);
+    d->msg_fp16 = prm->msg_precision == QLDPC_MSG_FP16;
+    d->kernel = prm->kernel == QLDPC_KERNEL_BASELINE ? QLDPC_KERNEL_BASELINE : QLDPC_KERNEL_FUSED;
+    d->prm.R = prm->legs_after_first;
+    d->prm.T1 = prm->iters_first;
+    d->prm.T2 = prm->iters_later;
+    d->prm.S = prm->stop_after_solutions;
+    d->prm.warm_mode = prm->warm_start_mode;
+    d->prm.max_iters = prm->max_total_iters;
+    d->prm.clip = prm->llr_clip > 0.0f ? prm->llr_clip : (d->msg_fp16 ? 65504.0f : 1e30f);
+
+    // prior LLRs w_j = log((1 - p_j) / p_j), computed in double and rounded once
+    std::vector<float> w(N);
+    for (int j = 0; j < N; ++j) w[j] = (float)std::log((1.0 - priors[j]) / priors[j]);
+
+    rc = d->kernel == QLDPC_KERNEL_BASELINE
+             ? setup_baseline(d, row_ptr, col_idx, w, prm->gamma_table)
+             : setup_fused(d, row_ptr, col_idx, w, prm->gamma_table, prm->block_threads);
+    if (rc == QLDPC_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) rc = fail(QLDPC_ERR_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
+    }
+    if (rc != QLDPC_OK) {
+        std::string msg = g_last_error;
+        qldpc_destroy(d);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = d;
+    return QLDPC_OK;
+}
+
+int qldpc_decode_batch(qldpc_decoder *d, const uint64_t *syndromes, int64_t B,
+                       uint64_t *corrections, int32_t *legs_used, uint8_t *converged,
+                       int32_t *iters, void *stream) {
+    g_last_error.clear();
+    int rc = check_batch(d, syndromes, B, corrections);
+    if (rc) return rc;
+    if (B == 0) return QLDPC_OK;
+    DeviceGuard guard(d->device);
+    QL_CUDA(guard.err);
+    const void *ptrs[5] = {syndromes, corrections, legs_used, converged, iters};
+    for (int q = 0; q < 5; ++q)
+        if (ptrs[q] && !is_device_ptr(ptrs[q]))
+            return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
+    return launch(d, syndromes, B, DecodeOut{corrections, legs_used, converged, iters},
+                  static_cast<cudaStream_t>(stream));
+}
+
+int qldpc_decode_batch_host(qldpc_decoder *d, const uint64_t *syndromes, int64_t B,
+                            uint64_t *corrections, int32_t *legs_used, uint8_t *converged,
+                            int32_t *iters) {
+    g_last_error.clear();
+    int rc = check_batch(d, syndromes, B, corrections);
+    if (rc) return rc;
+    if (B == 0) return QLDPC_OK;
+    DeviceGuard guard(d->device);
+    QL_CUDA(guard.err);
+    const int sw = (d->M + 63) / 64, cw = (d->N + 63) / 64;
+    const size_t s_syn = align_up(8 * (size_t)sw * B, 256), s_cor = align_up(8 * (size_t)cw * B, 256);
+    const size_t s_i32 = align_up(4 * (size_t)B, 256), s_u8 = align_up((size_t)B, 256);
+    if (B > d->stage_B) {
+        if (d->stage) QL_CUDA(cudaFree(d->stage));
+        d->stage = nullptr;
+        d->stage_B = 0;
+        QL_CUDA(cudaMalloc(&d->stage, s_syn + s_cor + 2 * s_i32 + s_u8));
+        d->stage_B = B;
+    }
+    char *base = static_cast<char *>(d->stage);
+    uint64_t *dsyn = reinterpret_cast<uint64_t *>(base);
+    uint64_t *dcor = reinterpret_cast<uint64_t *>(base + s_syn);
+    int32_t *dlegs = reinterpret_cast<int32_t *>(base + s_syn + s_cor);
+    int32_t *diters = reinterpret_cast<int32_t *>(base + s_syn + s_cor + s_i32);
+    uint8_t *dconv = reinterpret_cast<uint8_t *>(base + s_syn + s_cor + 2 * s_i32);
+    cudaStream_t st = d->stream;
+    QL_CUDA(cudaMemcpyAsync(dsyn, syndromes, 8 * (size_t)sw * B, cudaMemcpyHostToDevice, st));
+    rc = launch(d, dsyn, B, DecodeOut{dcor, legs_used ? dlegs : nullptr, converged ? dconv : nullptr,
+                                      iters ? diters : nullptr}, st);
+    if (rc) return rc;
+    QL_CUDA(cudaMemcpyAsync(corrections, dcor, 8 * (size_t)cw * B, cudaMemcpyDeviceToHost, st));
+    if (legs_used) QL_CUDA(cudaMemcpyAsync(legs_used, dlegs, 4 * (size_t)B, cudaMemcpyDeviceToHost, st));
+    if (iters) QL_CUDA(cudaMemcpyAsync(iters, diters, 4 * (size_t)B, cudaMemcpyDeviceToHost, st));
+    if (converged) QL_CUDA(cudaMemcpyAsync(converged, dconv, (size_t)B, cudaMemcpyDeviceToHost, st));
+    QL_CUDA(cudaStreamSynchronize(st));
+    return QLDPC_OK;
+}
+
+int qldpc_trace_first_leg(qldpc_decoder *d, const uint64_t *syndromes, int64_t B, int32_t T,
+                          float *marginals, float *nu, float *mu, void *stream) {
+    g_last_error.clear();
+    if (!d) return fail(QLDPC_ERR_INVALID_ARG, "decoder handle is NULL");
+    if (d->kernel != QLDPC_KERNEL_FUSED || !d->fk_trace)
+        return fail(QLDPC_ERR_UNSUPPORTED, "tracing needs the fused kernel");
+    if (B < 0 || B > 0x7fffffffLL || T < 0) return fail(QLDPC_ERR_INVALID_ARG, "bad B or T");
+    if (B == 0 || T == 0) return QLDPC_OK;
+    if (!syndromes) return fail(QLDPC_ERR_INVALID_ARG, "syndromes must not be NULL");
+    DeviceGuard guard(d->device);
+    QL_CUDA(guard.err);
+    const void *ptrs[4] = {syndromes, marginals, nu, mu};
+    for (int q = 0; q < 4; ++q)
+        if (ptrs[q] && !is_device_ptr(ptrs[q]))
+            return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
+    QL_CUDA(d->fk_trace->launch_trace(dim3((unsigned)B), d->trace_smem,
+                                      static_cast<cudaStream_t>(stream), d->fg, d->prm,
+                                      syndromes, (int)B, T, marginals, nu, mu));
+    return QLDPC_OK;
+}
+
+int qldpc_get_info(const qldpc_decoder *d, qldpc_info *info) {
+    if (!d || !info) return fail(QLDPC_ERR_INVALID_ARG, "NULL argument");
+    info->M = d->M;
+    info->N = d->N;
+    info->E = d->E;
+    info->max_check_degree = d->dc_max;
+    info->max_fault_degree = d->dv_max;
+    info->kernel = d->kernel;
+    info->msg_precision = d->msg_fp16 ? QLDPC_MSG_FP16 : QLDPC_MSG_FP32;
+    info->block_threads = d->block_threads;
+    info->blocks_per_sm = d->blocks_per_sm;
+    info->num_sms = d->num_sms;
+    info->grid_blocks = d->grid;
+    info->smem_bytes = (int32_t)d->smem;
+    info->syndrome_words = (d->M + 63) / 64;
+    info->correction_words = (d->N + 63) / 64;
+    return QLDPC_OK;
+}
+
+void qldpc_destroy(qldpc_decoder *d) {
+    if (!d) return;
+    DeviceGuard guard(d->device);
+    if (d->stream) {
+        cudaStreamSynchronize(d->stream);
+        cudaStreamDestroy(d->stream);
+    }
+    if (d->arena) cudaFree(d->arena);  // cudaFree waits for work that may still use it
+    if (d->stage) cudaFree(d->stage);
+    delete d;
+}
+
+const char *qldpc_status_string(int status) {
+    switch (status) {
+        case QLDPC_OK: return "ok";
+        case QLDPC_ERR_INVALID_ARG: return "invalid argument";
+        case QLDPC_ERR_CUDA: return "CUDA error";
+        case QLDPC_ERR_OOM: return "out of memory";
+        case QLDPC_ERR_UNSUPPORTED: return "unsupported graph or configuration";
+        default: return "unknown status";
+    }
+}
+
+const char *qldpc_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

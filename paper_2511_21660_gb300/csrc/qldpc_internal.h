@@ -1,0 +1,96 @@
+// Internal declarations shared by the host API and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qldpc {
+
+// Relay parameters as the kernels see them (paper App. A.3 naming).
+struct DevParams {
+    int R;                 // relay legs after the first
+    int T1, T2;            // iteration limits of the first and later legs
+    int S;                 // stop after S solutions
+    int warm_mode;         // 0: lambda(0) <- terminal marginals; 1: lambda(0) = w
+    long long max_iters;   // budget over all legs (<= 0: none)
+    float clip;            // saturation bound C
+};
+
+// Tanner graph in the layouts of the fused kernel.
+//   Slot (k, i) = k * Mp + i holds the message on the k-th edge of check i
+//   (edges of a check in increasing fault order); Mp = M rounded up to 32 so
+//   that a warp reading slot k of 32 consecutive checks hits 32 banks.
+struct FusedGraph {
+    int M, N, E, Mp;
+    int syn_words;        // ceil(M/64) uint64 words per syndrome
+    int cor_words;        // ceil(N/64) uint64 words per correction
+    int f_words;          // uint32 words of the decision bitmap (2*cor_words + 2)
+    const uint8_t *chk_deg;   // [M]
+    const int32_t *chk_col;   // [M][DC] fault of each slot, N for padding slots
+    const uint8_t *var_deg;   // [N]
+    const int32_t *var_slot;  // [N][DV] slots of the edges of fault j, increasing check order
+    const float *w;           // [N] prior LLRs
+    const float *gamma;       // [(R+1)][N]
+    const int32_t *slot_edge; // [DC*Mp] CSR edge id of each slot, -1 for padding (trace only)
+};
+
+// CSR/CSC graph of the plain baseline kernel.
+struct BaseGraph {
+    int M, N, E;
+    int syn_words, cor_words;
+    const int32_t *row_ptr;    // [M+1]
+    const int32_t *col_idx;    // [E]
+    const int32_t *var_ptr;    // [N+1]
+    const int32_t *var_edges;  // [E] edges of fault j in increasing edge order
+    const float *w;            // [N]
+    const float *gamma;        // [(R+1)][N]
+};
+
+struct DecodeOut {
+    uint64_t *corr;
+    int32_t *legs;
+    uint8_t *conv;
+    int32_t *iters;
+};
+
+// One compiled instance of the fused kernel.
+struct FusedKernel {
+    int msg_fp16;   // 0 float32 storage, 1 binary16 storage
+    int threads;    // NT
+    int vpt;        // faults per thread (register-resident)
+    int dc, dv;     // max check / fault degree supported
+    const void *decode_fn;   // __global__ symbol of the decode kernel
+    cudaError_t (*launch_decode)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
+                                 const DevParams &p, const uint64_t *syn, int B, DecodeOut out,
+                                 unsigned int *counter);
+    const void *trace_fn;    // __global__ symbol of the trace kernel (nullptr if none)
+    cudaError_t (*launch_trace)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
+                                const DevParams &p, const uint64_t *syn, int B, int T,
+                                float *marg, float *nu, float *mu);
+};
+
+// Shared memory of the fused kernels for a graph (bytes).
+inline size_t fused_smem_bytes(int Mp, int dc, int msg_bytes, int f_words, int syn_words) {
+    size_t msg = (size_t)dc * Mp * msg_bytes;
+    msg = (msg + 15) & ~(size_t)15;
+    return msg + 4 * (size_t)f_words + 8 * (size_t)syn_words + 64;
+}
+
+// Tables of compiled fused kernels, one per (precision, DC, DV) translation unit.
+#define QLDPC_DECLARE_TABLE(P, DC, DV) \
+    void fused_table_##P##_##DC##_##DV(const FusedKernel **out, int *n);
+QLDPC_DECLARE_TABLE(f32, 8, 4)
+QLDPC_DECLARE_TABLE(f32, 16, 8)
+QLDPC_DECLARE_TABLE(f32, 32, 8)
+QLDPC_DECLARE_TABLE(f16, 8, 4)
+QLDPC_DECLARE_TABLE(f16, 16, 8)
+QLDPC_DECLARE_TABLE(f16, 32, 8)
+#undef QLDPC_DECLARE_TABLE
+
+// Baseline kernel (float32, one shot per block).
+size_t baseline_smem_bytes(int M, int N, int E);
+const void *baseline_fn();
+cudaError_t launch_baseline(int B, int threads, size_t smem, cudaStream_t st, const BaseGraph &g,
+                            const DevParams &p, const uint64_t *syn, DecodeOut out);
+
+}  // namespace qldpc

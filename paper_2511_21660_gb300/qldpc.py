@@ -1,0 +1,271 @@
+"""Python binding of libqldpc.so (the C ABI in include/qldpc.h).
+
+Argument marshalling only: every step of decoding runs in the library's CUDA
+kernels.  The functions keep the C names; ``RelayDecoder`` wraps them for
+PyTorch tensors (device memory and streams come from torch).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+QLDPC_OK = 0
+QLDPC_ERR_INVALID_ARG = -1
+QLDPC_ERR_CUDA = -2
+QLDPC_ERR_OOM = -3
+QLDPC_ERR_UNSUPPORTED = -4
+QLDPC_MSG_FP32 = 0
+QLDPC_MSG_FP16 = 1
+QLDPC_KERNEL_AUTO = 0
+QLDPC_KERNEL_BASELINE = 1
+QLDPC_KERNEL_FUSED = 2
+
+EXPORTED = ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
+            "qldpc_trace_first_leg", "qldpc_get_info", "qldpc_destroy", "qldpc_status_string",
+            "qldpc_last_error")
+
+
+class qldpc_relay_params(ctypes.Structure):
+    _fields_ = [
+        ("legs_after_first", ctypes.c_int32),
+        ("iters_first", ctypes.c_int32),
+        ("iters_later", ctypes.c_int32),
+        ("max_total_iters", ctypes.c_int64),
+        ("stop_after_solutions", ctypes.c_int32),
+        ("warm_start_mode", ctypes.c_int32),
+        ("msg_precision", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("llr_clip", ctypes.c_float),
+        ("gamma_table", ctypes.c_void_p),
+    ]
+
+
+class qldpc_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "M", "N", "E", "max_check_degree", "max_fault_degree", "kernel", "msg_precision",
+        "block_threads", "blocks_per_sm", "num_sms", "grid_blocks", "smem_bytes",
+        "syndrome_words", "correction_words")]
+
+
+class QldpcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status}): {last_error()}")
+        self.status = status
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libqldpc.so (built in-tree by __graft_entry__.build()); raise if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libqldpc.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.qldpc_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, P, P, P,
+                                 ctypes.POINTER(qldpc_relay_params), ctypes.c_int]
+    lib.qldpc_decode_batch.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P]
+    lib.qldpc_decode_batch_host.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
+    lib.qldpc_trace_first_leg.argtypes = [P, P, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
+    lib.qldpc_get_info.argtypes = [P, ctypes.POINTER(qldpc_info)]
+    lib.qldpc_destroy.argtypes = [P]
+    lib.qldpc_destroy.restype = None
+    lib.qldpc_status_string.argtypes = [ctypes.c_int]
+    lib.qldpc_status_string.restype = ctypes.c_char_p
+    lib.qldpc_last_error.argtypes = []
+    lib.qldpc_last_error.restype = ctypes.c_char_p
+    for name in ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
+                 "qldpc_trace_first_leg", "qldpc_get_info"):
+        getattr(lib, name).restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load_library().qldpc_status_string(status).decode()
+
+
+def last_error() -> str:
+    return load_library().qldpc_last_error().decode()
+
+
+def _check(status: int, what: str) -> None:
+    if status != QLDPC_OK:
+        raise QldpcError(status, what)
+
+
+# ---- thin wrappers with the C names --------------------------------------------------
+
+def qldpc_create(M, N, row_ptr, col_idx, priors, params: qldpc_relay_params, device=0):
+    """Returns an opaque handle (ctypes.c_void_p).  Inputs are numpy host arrays."""
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    pr = np.ascontiguousarray(priors, dtype=np.float64)
+    _check(lib.qldpc_create(ctypes.byref(h), int(M), int(N), rp.ctypes.data, ci.ctypes.data,
+                            pr.ctypes.data, ctypes.byref(params), int(device)), "qldpc_create")
+    return h
+
+
+def qldpc_decode_batch(h, syndromes_ptr, B, corrections_ptr, legs_ptr=None, conv_ptr=None,
+                       iters_ptr=None, stream=None):
+    _check(load_library().qldpc_decode_batch(h, syndromes_ptr, int(B), corrections_ptr,
+                                             legs_ptr, conv_ptr, iters_ptr, stream),
+           "qldpc_decode_batch")
+
+
+def qldpc_decode_batch_host(h, syndromes_ptr, B, corrections_ptr, legs_ptr=None, conv_ptr=None,
+                            iters_ptr=None):
+    _check(load_library().qldpc_decode_batch_host(h, syndromes_ptr, int(B), corrections_ptr,
+                                                  legs_ptr, conv_ptr, iters_ptr),
+           "qldpc_decode_batch_host")
+
+
+def qldpc_trace_first_leg(h, syndromes_ptr, B, T, marg_ptr=None, nu_ptr=None, mu_ptr=None,
+                          stream=None):
+    _check(load_library().qldpc_trace_first_leg(h, syndromes_ptr, int(B), int(T), marg_ptr,
+                                                nu_ptr, mu_ptr, stream),
+           "qldpc_trace_first_leg")
+
+
+def qldpc_get_info(h) -> qldpc_info:
+    info = qldpc_info()
+    _check(load_library().qldpc_get_info(h, ctypes.byref(info)), "qldpc_get_info")
+    return info
+
+
+def qldpc_destroy(h) -> None:
+    if h is not None and h.value:
+        load_library().qldpc_destroy(h)
+
+
+# ---- torch convenience wrapper ------------------------------------------------------
+
+@dataclass
+class RelayConfig:
+    """Relay parameters (paper App. A.3 defaults) plus kernel options."""
+    legs_after_first: int = 300
+    iters_first: int = 80
+    iters_later: int = 60
+    max_total_iters: int = 0
+    stop_after_solutions: int = 1
+    warm_start_mode: int = 0
+    msg_precision: int = QLDPC_MSG_FP32
+    kernel: int = QLDPC_KERNEL_AUTO
+    block_threads: int = 0
+    llr_clip: float = 0.0
+
+
+class RelayDecoder:
+    """A decoder for one decoding problem (H as CSR, priors, gamma table) on one GPU."""
+
+    def __init__(self, row_ptr, col_idx, priors, gamma_table, config: RelayConfig | None = None,
+                 device: int = 0):
+        cfg = config or RelayConfig()
+        self.config = cfg
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        self.M = row_ptr.size - 1
+        self.N = int(np.asarray(priors).size)
+        gam = np.ascontiguousarray(gamma_table, dtype=np.float32)
+        if gam.shape != (cfg.legs_after_first + 1, self.N):
+            raise ValueError(f"gamma table must be [{cfg.legs_after_first + 1}, {self.N}]")
+        self._gamma = gam
+        prm = qldpc_relay_params(cfg.legs_after_first, cfg.iters_first, cfg.iters_later,
+                                 cfg.max_total_iters, cfg.stop_after_solutions,
+                                 cfg.warm_start_mode, cfg.msg_precision, cfg.kernel,
+                                 cfg.block_threads, cfg.llr_clip, gam.ctypes.data)
+        self.device = device
+        self.handle = qldpc_create(self.M, self.N, row_ptr, col_idx, priors, prm, device)
+        self.info = qldpc_get_info(self.handle)
+        self.syndrome_words = self.info.syndrome_words
+        self.correction_words = self.info.correction_words
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            qldpc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream_ptr(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def outputs(self, B: int):
+        import torch
+        dev = torch.device("cuda", self.device)
+        return (torch.empty((B, self.correction_words), dtype=torch.int64, device=dev),
+                torch.empty(B, dtype=torch.int32, device=dev),
+                torch.empty(B, dtype=torch.uint8, device=dev),
+                torch.empty(B, dtype=torch.int32, device=dev))
+
+    def decode(self, syndromes, out=None, stream=None):
+        """syndromes: int64 CUDA tensor [B, ceil(M/64)] (bit-packed uint64 words).
+
+        Returns (corrections int64 [B, ceil(N/64)], legs int32 [B], converged uint8 [B],
+        iters int32 [B]), all on the device, enqueued on ``stream`` (default: torch's
+        current stream).
+        """
+        if not syndromes.is_cuda or syndromes.dim() != 2 or \
+                syndromes.shape[1] != self.syndrome_words or not syndromes.is_contiguous():
+            raise ValueError("syndromes must be a contiguous CUDA tensor [B, ceil(M/64)]")
+        B = syndromes.shape[0]
+        cor, legs, conv, iters = out if out is not None else self.outputs(B)
+        qldpc_decode_batch(self.handle, ctypes.c_void_p(syndromes.data_ptr()), B,
+                           ctypes.c_void_p(cor.data_ptr()), ctypes.c_void_p(legs.data_ptr()),
+                           ctypes.c_void_p(conv.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
+                           self._stream_ptr(stream))
+        return cor, legs, conv, iters
+
+    def decode_host(self, syndromes: np.ndarray, out=None):
+        """Host-buffer path: numpy uint64 [B, ceil(M/64)] in, numpy arrays out (synchronous)."""
+        syn = np.ascontiguousarray(syndromes, dtype=np.uint64)
+        if syn.ndim != 2 or syn.shape[1] != self.syndrome_words:
+            raise ValueError("syndromes must be uint64 [B, ceil(M/64)]")
+        B = syn.shape[0]
+        if out is None:
+            out = (np.empty((B, self.correction_words), dtype=np.uint64),
+                   np.empty(B, dtype=np.int32), np.empty(B, dtype=np.uint8),
+                   np.empty(B, dtype=np.int32))
+        cor, legs, conv, iters = out
+        qldpc_decode_batch_host(self.handle, ctypes.c_void_p(syn.ctypes.data), B,
+                                ctypes.c_void_p(cor.ctypes.data), ctypes.c_void_p(legs.ctypes.data),
+                                ctypes.c_void_p(conv.ctypes.data),
+                                ctypes.c_void_p(iters.ctypes.data))
+        return out
+
+    def trace_first_leg(self, syndromes, T: int, messages: bool = True, stream=None):
+        """Lambda(t), nu(t), mu(t) for t = 1..T of the first leg (no early exit)."""
+        import torch
+        B = syndromes.shape[0]
+        dev = syndromes.device
+        marg = torch.empty((T, B, self.N), dtype=torch.float32, device=dev)
+        nu = torch.empty((T, B, self.info.E), dtype=torch.float32, device=dev) if messages else None
+        mu = torch.empty((T, B, self.info.E), dtype=torch.float32, device=dev) if messages else None
+        qldpc_trace_first_leg(self.handle, ctypes.c_void_p(syndromes.data_ptr()), B, T,
+                              ctypes.c_void_p(marg.data_ptr()),
+                              ctypes.c_void_p(nu.data_ptr()) if messages else None,
+                              ctypes.c_void_p(mu.data_ptr()) if messages else None,
+                              self._stream_ptr(stream))
+        return marg, nu, mu
