@@ -189,6 +189,35 @@ def timed_decode(dec, syn, out, steps, warmup, stream, flush):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def run_decode_only(args):
+    """Profiling driver: decode args.shots syndromes with one kernel configuration."""
+    import torch
+
+    from paper_2511_21660_gb300 import (QLDPC_KERNEL_BASELINE, QLDPC_KERNEL_FUSED,
+                                        QLDPC_MSG_FP16, QLDPC_MSG_FP32, RelayConfig, RelayDecoder)
+    P, sig, gam = make_inputs(args.shots, SEED)
+    dev = torch.device("cuda", 0)
+    syn = torch.from_numpy(pack_bits(sig).view(np.int64)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    cfg = RelayConfig(stop_after_solutions=S_SOLUTIONS,
+                      msg_precision=QLDPC_MSG_FP16 if args.msg == "fp16" else QLDPC_MSG_FP32,
+                      kernel=QLDPC_KERNEL_BASELINE if args.kernel == "baseline"
+                      else QLDPC_KERNEL_FUSED, block_threads=args.block_threads)
+    dec = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam, cfg)
+    out = dec.outputs(args.shots)
+    times = timed_decode(dec, syn, out, args.steps, args.warmup, stream, flush)
+    iters = int(out[3].sum().item())
+    ms = sum(times) / len(times)
+    print(json.dumps({"mode": "decode-only", "kernel": args.kernel, "msg": args.msg,
+                      "shots": args.shots, "ms_per_step": ms,
+                      "syndromes_per_s": args.shots / (ms / 1e3),
+                      "iterations": iters, "block_threads": dec.info.block_threads,
+                      "blocks_per_sm": dec.info.blocks_per_sm, "grid": dec.info.grid_blocks,
+                      "smem_bytes": dec.info.smem_bytes}), flush=True)
+    dec.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -340,9 +369,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--shots", type=int, default=SHOTS,
+                    help="syndromes per step (profiling runs use fewer)")
+    ap.add_argument("--only-decode", action="store_true",
+                    help="time the decode kernel only (no variants, e2e or CPU baseline)")
+    ap.add_argument("--kernel", choices=["fused", "baseline"], default="fused")
+    ap.add_argument("--msg", choices=["fp32", "fp16"], default="fp32")
+    ap.add_argument("--block-threads", type=int, default=0)
     args = ap.parse_args()
+    if (args.shots != SHOTS or args.kernel != "fused" or args.msg != "fp32"
+            or args.block_threads):
+        args.only_decode = True
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_decode:
+        run_decode_only(args)
     else:
         run_ours(args)
 

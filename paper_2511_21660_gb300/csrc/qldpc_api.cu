@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "qldpc.h"
 #include "qldpc_internal.h"
 
@@ -113,8 +115,9 @@ int validate_params(const qldpc_relay_params *p, int N) {
         return fail(QLDPC_ERR_INVALID_ARG, "unknown kernel %d", p->kernel);
     if (p->block_threads < 0) return fail(QLDPC_ERR_INVALID_ARG, "block_threads < 0");
     if (!(std::isfinite(p->llr_clip))) return fail(QLDPC_ERR_INVALID_ARG, "llr_clip is not finite");
-    if (p->msg_precision == QLDPC_MSG_FP16 && p->llr_clip > 65504.0f)
-        return fail(QLDPC_ERR_INVALID_ARG, "llr_clip above the binary16 range");
+    if (p->msg_precision == QLDPC_MSG_FP16 && p->llr_clip > 0.0f &&
+        __half2float(__float2half_rn(p->llr_clip)) != p->llr_clip)
+        return fail(QLDPC_ERR_INVALID_ARG, "llr_clip must be a binary16 value (<= 65504)");
     if (!p->gamma_table) return fail(QLDPC_ERR_INVALID_ARG, "gamma_table must not be NULL");
     const size_t n = (size_t)(p->legs_after_first + 1) * N;
     for (size_t q = 0; q < n; ++q)
@@ -173,9 +176,11 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
     g.cor_words = (N + 63) / 64;
     g.f_words = 2 * g.cor_words + 2;
 
-    std::vector<uint8_t> chk_deg(M), var_deg(N, 0);
+    std::vector<uint8_t> chk_deg(g.Mp, 0);
+    std::vector<int> var_deg(N, 0);
     std::vector<int32_t> chk_col((size_t)M * DC, N), var_slot((size_t)N * DV, 0);
     std::vector<int32_t> slot_edge((size_t)DC * g.Mp, -1);
+    std::vector<uint32_t> pad_mask((size_t)(g.Mp / 2) * DC, 0);
     for (int i = 0; i < M; ++i) {
         chk_deg[i] = (uint8_t)(row_ptr[i + 1] - row_ptr[i]);
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
@@ -186,7 +191,10 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
             var_slot[(size_t)j * DV + var_deg[j]++] = slot;  // rows ascending => checks ascending
         }
     }
-
+    for (int j = 0; j < N; ++j) var_slot[(size_t)j * DV] |= var_deg[j] << 24;
+    for (int i = 0; i < g.Mp; ++i)
+        for (int k = chk_deg[i]; k < DC; ++k)
+            pad_mask[(size_t)(i / 2) * DC + k] |= (i & 1) ? 0xffff0000u : 0x0000ffffu;
     const int msg_bytes = d->msg_fp16 ? 2 : 4;
     d->smem = fused_smem_bytes(g.Mp, DC, msg_bytes, g.f_words, g.syn_words);
     int optin = 0;
@@ -212,7 +220,7 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
     // one device arena for every graph array
     const size_t R1 = (size_t)d->prm.R + 1;
     size_t off[8], o = 0;
-    const size_t sizes[8] = {(size_t)M, sizeof(int32_t) * M * DC, (size_t)N,
+    const size_t sizes[8] = {(size_t)g.Mp, sizeof(int32_t) * M * DC, sizeof(uint32_t) * pad_mask.size(),
                              sizeof(int32_t) * N * DV, sizeof(float) * N, sizeof(float) * R1 * N,
                              sizeof(int32_t) * DC * g.Mp, sizeof(unsigned int) * 4};
     for (int q = 0; q < 8; ++q) {
@@ -221,13 +229,13 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
     }
     QL_CUDA(cudaMalloc(&d->arena, o));
     char *base = static_cast<char *>(d->arena);
-    const void *src[7] = {chk_deg.data(), chk_col.data(), var_deg.data(), var_slot.data(),
+    const void *src[7] = {chk_deg.data(), chk_col.data(), pad_mask.data(), var_slot.data(),
                           w.data(), gamma, slot_edge.data()};
     for (int q = 0; q < 7; ++q)
         QL_CUDA(cudaMemcpy(base + off[q], src[q], sizes[q], cudaMemcpyHostToDevice));
     g.chk_deg = reinterpret_cast<const uint8_t *>(base + off[0]);
     g.chk_col = reinterpret_cast<const int32_t *>(base + off[1]);
-    g.var_deg = reinterpret_cast<const uint8_t *>(base + off[2]);
+    g.pad_mask = reinterpret_cast<const uint32_t *>(base + off[2]);
     g.var_slot = reinterpret_cast<const int32_t *>(base + off[3]);
     g.w = reinterpret_cast<const float *>(base + off[4]);
     g.gamma = reinterpret_cast<const float *>(base + off[5]);

@@ -25,10 +25,12 @@ struct FusedGraph {
     int syn_words;        // ceil(M/64) uint64 words per syndrome
     int cor_words;        // ceil(N/64) uint64 words per correction
     int f_words;          // uint32 words of the decision bitmap (2*cor_words + 2)
-    const uint8_t *chk_deg;   // [M]
+    const uint8_t *chk_deg;   // [Mp] check degrees (0 for rows M..Mp-1)
     const int32_t *chk_col;   // [M][DC] fault of each slot, N for padding slots
-    const uint8_t *var_deg;   // [N]
-    const int32_t *var_slot;  // [N][DV] slots of the edges of fault j, increasing check order
+    const int32_t *var_slot;  // [N][DV] slots of the edges of fault j, increasing check
+                              // order; the top byte of entry 0 holds the fault degree
+    const uint32_t *pad_mask; // [Mp/2][DC] binary16 only: 0xffff in the half of the
+                              // check pair's word whose slot k is padding
     const float *w;           // [N] prior LLRs
     const float *gamma;       // [(R+1)][N]
     const int32_t *slot_edge; // [DC*Mp] CSR edge id of each slot, -1 for padding (trace only)
@@ -57,6 +59,7 @@ struct DecodeOut {
 struct FusedKernel {
     int msg_fp16;   // 0 float32 storage, 1 binary16 storage
     int threads;    // NT
+    int min_blocks; // launch-bounds residency target
     int vpt;        // faults per thread (register-resident)
     int dc, dv;     // max check / fault degree supported
     const void *decode_fn;   // __global__ symbol of the decode kernel

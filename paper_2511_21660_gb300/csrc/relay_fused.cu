@@ -51,22 +51,36 @@ struct Msg<__half> {
 
 __device__ __forceinline__ float clampc(float x, float c) { return fminf(fmaxf(x, -c), c); }
 
-__device__ __forceinline__ uint32_t fbit(const uint32_t *fw, int j) {
-    return (fw[j >> 5] >> (j & 31)) & 1u;
+// Per-fault edge list: DV slot indices, the first one carrying the fault degree
+// in its top byte (slot indices are below 2^24).
+template <int DV>
+__device__ __forceinline__ int load_slots(const FusedGraph &g, int j, int (&sl)[DV]) {
+    const int4 *p = reinterpret_cast<const int4 *>(g.var_slot + (size_t)j * DV);
+    const int4 v = __ldg(p);
+    sl[0] = v.x & 0xffffff;
+    sl[1] = v.y;
+    sl[2] = v.z;
+    sl[3] = v.w;
+    const int deg = (int)((unsigned)v.x >> 24);
+#pragma unroll
+    for (int q = 1; q < DV / 4; ++q) {
+        if (deg > 4 * q) {
+            const int4 u = __ldg(p + q);
+            sl[4 * q] = u.x;
+            sl[4 * q + 1] = u.y;
+            sl[4 * q + 2] = u.z;
+            sl[4 * q + 3] = u.w;
+        } else {
+            sl[4 * q] = sl[4 * q + 1] = sl[4 * q + 2] = sl[4 * q + 3] = 0;
+        }
+    }
+    return deg;
 }
 
-template <int DV>
-__device__ __forceinline__ void load_slots(const FusedGraph &g, int j, int (&sl)[DV]) {
-    const int4 *p = reinterpret_cast<const int4 *>(g.var_slot + (size_t)j * DV);
-#pragma unroll
-    for (int q = 0; q < DV / 4; ++q) {
-        const int4 v = __ldg(p + q);
-        sl[4 * q] = v.x;
-        sl[4 * q + 1] = v.y;
-        sl[4 * q + 2] = v.z;
-        sl[4 * q + 3] = v.w;
-    }
-}
+// Messages are stored with zeros canonicalised to +0 (x + 0 = x for x != 0 and
+// -0 + 0 = +0), so that the check pass may take the sign of a stored message from
+// its sign bit: sign(x) = -1 iff x < 0 then holds bit for bit.
+__device__ __forceinline__ float canon(float x) { return __fadd_rn(x, 0.0f); }
 
 // Start of a leg: lambda(0), Lambda(0), nu(0) and the leg's memory strengths.
 //   leg 0:  lambda(0) = Lambda(0) = w
@@ -82,63 +96,146 @@ __device__ __forceinline__ void leg_init(const FusedGraph &g, const DevParams &p
     for (int r = 0; r < VPT; ++r) {
         const int j = threadIdx.x + r * NT;
         if (j < g.N) {
-            const float wj = __ldg(g.w + j);
-            const float lam0 = (leg == 0 || p.warm_mode == 1) ? wj : Lam[r];
+            const float lam0 = (leg == 0 || p.warm_mode == 1) ? __ldg(g.w + j) : Lam[r];
             if (leg == 0) Lam[r] = lam0;
             const float gm = __ldg(grow + j);
             gg[r] = gm;
             bb[r] = __fmul_rn(__fsub_rn(1.0f, gm), lam0);
-            const int deg = g.var_deg[j];
             int sl[DV];
-            load_slots<DV>(g, j, sl);
+            const int deg = load_slots<DV>(g, j, sl);
+            const float nu0 = canon(lam0);
 #pragma unroll
             for (int k = 0; k < DV; ++k)
-                if (k < deg) Msg<MT>::st(msg + sl[k], lam0);
+                if (k < deg) Msg<MT>::st(msg + sl[k], nu0);
         }
     }
 }
 
-// Check pass: mu_{i->j}(t) from nu(t-1) for every check, in place.
-// min over the excluded set via the two smallest magnitudes; the padding slots
-// of a check hold C, which is also the min over an empty set.
-template <typename MT, int NT, int DC>
-__device__ __forceinline__ void check_pass(const FusedGraph &g, MT *msg, const uint32_t *sg,
+// Check pass, float32 messages: mu_{i->j}(t) from nu(t-1) for every check, in place.
+// (m1, m2) = the two smallest magnitudes of the check's slots (with multiplicity),
+// so the min over the excluded set of slot k is m2 if |nu_k| = m1, else m1.
+// Padding slots hold C, which is also the min over an empty set, and are never
+// written.  The sign is (-1)^sigma_i times the product of all signs times sign(nu_k).
+template <int NT, int DC>
+__device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, const uint32_t *sg,
                                            float C) {
     for (int i = threadIdx.x; i < g.M; i += NT) {
-        const uint32_t s = (sg[i >> 5] >> (i & 31)) & 1u;
         const int deg = g.chk_deg[i];
+        uint32_t sx = sg[i >> 5] << (31 - (i & 31));
         float v[DC];
 #pragma unroll
-        for (int k = 0; k < DC; ++k) v[k] = Msg<MT>::ld(msg + k * g.Mp + i);
+        for (int k = 0; k < DC; ++k) v[k] = msg[k * g.Mp + i];
         float m1 = C, m2 = C;
-        int am = -1;
-        uint32_t neg = s, sb = 0;
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
             const float a = fabsf(v[k]);
-            const uint32_t sk = v[k] < 0.0f ? 1u : 0u;
-            sb |= sk << k;
-            neg ^= sk;
-            if (a < m1) {
-                m2 = m1;
-                m1 = a;
-                am = k;
-            } else if (a < m2) {
-                m2 = a;
-            }
+            m2 = fminf(m2, fmaxf(m1, a));
+            m1 = fminf(m1, a);
+            sx ^= __float_as_uint(v[k]);
         }
+        sx &= 0x80000000u;
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
-            const float mag = (k == am) ? m2 : m1;
-            float o = ((neg ^ (sb >> k)) & 1u) ? -mag : mag;
-            if (k >= deg) o = C;
-            Msg<MT>::st(msg + k * g.Mp + i, o);
+            if (k < deg) {
+                const float mag = (fabsf(v[k]) <= m1) ? m2 : m1;
+                msg[k * g.Mp + i] = __uint_as_float(__float_as_uint(mag) |
+                                                    ((sx ^ __float_as_uint(v[k])) & 0x80000000u));
+            }
         }
     }
 }
 
-// Fault pass: memory update, marginals, fault->check messages (explicit excluded
-// sums, in increasing check order), decisions into the bitmap.
+// Check pass, binary16 messages: two checks (2q, 2q+1) per thread with half2
+// arithmetic (min, max and sign manipulation are exact in any format).  A 32-bit
+// word of slot k holds both checks; a per-pair mask keeps C in padding lanes.
+template <int NT, int DC>
+__device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, const uint32_t *sg,
+                                           float C) {
+    uint32_t *w32 = reinterpret_cast<uint32_t *>(msg);
+    const int Mp2 = g.Mp >> 1, M2 = (g.M + 1) >> 1;
+    const __half2 C2 = __float2half2_rn(C);
+    const uint32_t c2 = *reinterpret_cast<const uint32_t *>(&C2);
+    for (int q = threadIdx.x; q < M2; q += NT) {
+        const int i = 2 * q;
+        const uint32_t sb = (sg[i >> 5] >> (i & 31)) & 3u;
+        uint32_t sx = ((sb & 1u) << 15) | ((sb & 2u) << 30);
+        uint32_t v[DC];
+#pragma unroll
+        for (int k = 0; k < DC; ++k) v[k] = w32[k * Mp2 + q];
+        __half2 m1 = C2, m2 = C2;
+#pragma unroll
+        for (int k = 0; k < DC; ++k) {
+            const __half2 a = __habs2(*reinterpret_cast<const __half2 *>(&v[k]));
+            m2 = __hmin2(m2, __hmax2(m1, a));
+            m1 = __hmin2(m1, a);
+            sx ^= v[k];
+        }
+        sx &= 0x80008000u;
+        const uint32_t u1 = *reinterpret_cast<const uint32_t *>(&m1);
+        const uint32_t u2 = *reinterpret_cast<const uint32_t *>(&m2);
+        const uint4 *pm4 = reinterpret_cast<const uint4 *>(g.pad_mask + (size_t)q * DC);
+        uint32_t pm[DC];
+#pragma unroll
+        for (int k4 = 0; k4 < DC / 4; ++k4) {
+            const uint4 t = __ldg(pm4 + k4);
+            pm[4 * k4] = t.x;
+            pm[4 * k4 + 1] = t.y;
+            pm[4 * k4 + 2] = t.z;
+            pm[4 * k4 + 3] = t.w;
+        }
+#pragma unroll
+        for (int k = 0; k < DC; ++k) {
+            const __half2 a = __habs2(*reinterpret_cast<const __half2 *>(&v[k]));
+            const uint32_t eq = __hle2_mask(a, m1);
+            const uint32_t mag = (u2 & eq) | (u1 & ~eq);
+            const uint32_t o = mag | ((sx ^ v[k]) & 0x80008000u);
+            w32[k * Mp2 + q] = (o & ~pm[k]) | (c2 & pm[k]);
+        }
+    }
+}
+
+// Fault update for one fault: memory term, marginal, excluded sums (increasing check
+// order, one rounding per addition, exactly as written in the oracle).
+template <typename MT, int DV>
+__device__ __forceinline__ float fault_update(MT *msg, const int (&sl)[DV], int deg, float lam,
+                                              float C) {
+    if (deg == 3) {
+        const float mu0 = Msg<MT>::ld(msg + sl[0]), mu1 = Msg<MT>::ld(msg + sl[1]),
+                    mu2 = Msg<MT>::ld(msg + sl[2]);
+        const float s0 = __fadd_rn(lam, mu0), s01 = __fadd_rn(s0, mu1);
+        Msg<MT>::st(msg + sl[0], canon(clampc(__fadd_rn(__fadd_rn(lam, mu1), mu2), C)));
+        Msg<MT>::st(msg + sl[1], canon(clampc(__fadd_rn(s0, mu2), C)));
+        Msg<MT>::st(msg + sl[2], canon(clampc(s01, C)));
+        return clampc(__fadd_rn(s01, mu2), C);
+    }
+    if (deg == 2) {
+        const float mu0 = Msg<MT>::ld(msg + sl[0]), mu1 = Msg<MT>::ld(msg + sl[1]);
+        const float s0 = __fadd_rn(lam, mu0);
+        Msg<MT>::st(msg + sl[0], canon(clampc(__fadd_rn(lam, mu1), C)));
+        Msg<MT>::st(msg + sl[1], canon(clampc(s0, C)));
+        return clampc(__fadd_rn(s0, mu1), C);
+    }
+    float mu[DV];
+#pragma unroll
+    for (int k = 0; k < DV; ++k) mu[k] = (k < deg) ? Msg<MT>::ld(msg + sl[k]) : 0.0f;
+    float L = lam;
+#pragma unroll
+    for (int k = 0; k < DV; ++k)
+        if (k < deg) L = __fadd_rn(L, mu[k]);
+#pragma unroll
+    for (int k = 0; k < DV; ++k) {
+        if (k < deg) {
+            float v = lam;
+#pragma unroll
+            for (int k2 = 0; k2 < DV; ++k2)
+                if (k2 != k && k2 < deg) v = __fadd_rn(v, mu[k2]);
+            Msg<MT>::st(msg + sl[k], canon(clampc(v, C)));
+        }
+    }
+    return clampc(L, C);
+}
+
+// Fault pass: memory update, marginals, fault->check messages, decisions into the bitmap.
 template <typename MT, int NT, int VPT, int DV>
 __device__ __forceinline__ void fault_pass(const FusedGraph &g, MT *msg, uint32_t *fw,
                                            float (&Lam)[VPT], const float (&bb)[VPT],
@@ -151,27 +248,9 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, MT *msg, uint32_
         float L = 0.0f;
         if (valid) {
             const float lam = __fadd_rn(bb[r], __fmul_rn(gg[r], Lam[r]));
-            const int deg = g.var_deg[j];
             int sl[DV];
-            load_slots<DV>(g, j, sl);
-            float mu[DV];
-#pragma unroll
-            for (int k = 0; k < DV; ++k) mu[k] = (k < deg) ? Msg<MT>::ld(msg + sl[k]) : 0.0f;
-            L = lam;
-#pragma unroll
-            for (int k = 0; k < DV; ++k)
-                if (k < deg) L = __fadd_rn(L, mu[k]);
-            L = clampc(L, C);
-#pragma unroll
-            for (int k = 0; k < DV; ++k) {
-                if (k < deg) {
-                    float v = lam;
-#pragma unroll
-                    for (int k2 = 0; k2 < DV; ++k2)
-                        if (k2 != k && k2 < deg) v = __fadd_rn(v, mu[k2]);
-                    Msg<MT>::st(msg + sl[k], clampc(v, C));
-                }
-            }
+            const int deg = load_slots<DV>(g, j, sl);
+            L = fault_update<MT, DV>(msg, sl, deg, lam, C);
             Lam[r] = L;
         }
         const uint32_t bal = __ballot_sync(FULL, valid && L < 0.0f);
@@ -181,19 +260,23 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, MT *msg, uint32_
 }
 
 // H F = sigma ?  Returns true (in every thread) when some check is unsatisfied.
+// Padding slots name fault N, whose decision bit is always 0.
 template <int NT, int DC>
 __device__ __forceinline__ bool syndrome_unsat(const FusedGraph &g, const uint32_t *fw,
                                                const uint32_t *sg) {
     uint32_t bad = 0;
     for (int i = threadIdx.x; i < g.M; i += NT) {
-        uint32_t par = (sg[i >> 5] >> (i & 31)) & 1u;
+        uint32_t par = sg[i >> 5] >> (i & 31);
         const int4 *c4 = reinterpret_cast<const int4 *>(g.chk_col + (size_t)i * DC);
 #pragma unroll
         for (int q = 0; q < DC / 4; ++q) {
             const int4 c = __ldg(c4 + q);
-            par ^= fbit(fw, c.x) ^ fbit(fw, c.y) ^ fbit(fw, c.z) ^ fbit(fw, c.w);
+            const uint32_t wx = fw[c.x >> 5], wy = fw[c.y >> 5], wz = fw[c.z >> 5],
+                           ww = fw[c.w >> 5];
+            par ^= __funnelshift_r(wx, wx, c.x) ^ __funnelshift_r(wy, wy, c.y) ^
+                   __funnelshift_r(wz, wz, c.z) ^ __funnelshift_r(ww, ww, c.w);
         }
-        bad |= par;
+        bad |= par & 1u;
     }
     return __syncthreads_or(bad) != 0;
 }
@@ -239,7 +322,7 @@ __device__ __forceinline__ void smem_layout(const FusedGraph &g, unsigned char *
 template <typename MT, int NT, int DC>
 __device__ __forceinline__ void block_setup(const FusedGraph &g, MT *msg, uint32_t *fw, float C) {
     for (int q = threadIdx.x; q < g.f_words; q += NT) fw[q] = 0u;
-    for (int i = threadIdx.x; i < g.M; i += NT) {
+    for (int i = threadIdx.x; i < g.Mp; i += NT) {
         const int deg = g.chk_deg[i];
         for (int k = deg; k < DC; ++k) Msg<MT>::st(msg + k * g.Mp + i, C);
     }
@@ -255,8 +338,8 @@ __device__ __forceinline__ void load_syndrome(const FusedGraph &g, const uint64_
     }
 }
 
-template <typename MT, int NT, int VPT, int DC, int DV>
-__global__ void __launch_bounds__(NT) fused_decode(FusedGraph g, DevParams p,
+template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
+__global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams p,
                                                    const uint64_t *__restrict__ syn, int B,
                                                    DecodeOut out, unsigned int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -291,7 +374,7 @@ __global__ void __launch_bounds__(NT) fused_decode(FusedGraph g, DevParams p,
         for (;;) {
             const int T = leg == 0 ? p.T1 : p.T2;
             for (int t = 1; t <= T; ++t) {
-                check_pass<MT, NT, DC>(g, msg, sg, C);
+                check_pass<NT, DC>(g, msg, sg, C);
                 __syncthreads();
                 fault_pass<MT, NT, VPT, DV>(g, msg, fw, Lam, bb, gg, C);
                 __syncthreads();
@@ -350,7 +433,7 @@ __global__ void __launch_bounds__(NT) fused_trace(FusedGraph g, DevParams p,
     const int nslots = DC * g.Mp;
     for (int t = 0; t < T; ++t) {
         const size_t o = (size_t)t * B + shot;
-        check_pass<MT, NT, DC>(g, msg, sg, C);
+        check_pass<NT, DC>(g, msg, sg, C);
         __syncthreads();
         if (mu)
             for (int s = threadIdx.x; s < nslots; s += NT) {
@@ -376,11 +459,11 @@ __global__ void __launch_bounds__(NT) fused_trace(FusedGraph g, DevParams p,
     }
 }
 
-template <typename MT, int NT, int VPT, int DC, int DV>
+template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
 cudaError_t launch_decode(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                           const DevParams &p, const uint64_t *syn, int B, DecodeOut out,
                           unsigned int *counter) {
-    fused_decode<MT, NT, VPT, DC, DV><<<grid, NT, smem, st>>>(g, p, syn, B, out, counter);
+    fused_decode<MT, NT, VPT, MINB, DC, DV><<<grid, NT, smem, st>>>(g, p, syn, B, out, counter);
     return cudaGetLastError();
 }
 
@@ -398,18 +481,24 @@ using MsgT = __half;
 using MsgT = float;
 #endif
 
-template <int NT, int VPT, bool TRACE>
+template <int NT, int VPT, int MINB, bool TRACE>
 FusedKernel entry() {
     FusedKernel k;
     k.msg_fp16 = QL_MSG_F16;
     k.threads = NT;
+    k.min_blocks = MINB;
     k.vpt = VPT;
     k.dc = QL_DC;
     k.dv = QL_DV;
-    k.decode_fn = (const void *)fused_decode<MsgT, NT, VPT, QL_DC, QL_DV>;
-    k.launch_decode = &launch_decode<MsgT, NT, VPT, QL_DC, QL_DV>;
-    k.trace_fn = TRACE ? (const void *)fused_trace<MsgT, NT, VPT, QL_DC, QL_DV> : nullptr;
-    k.launch_trace = TRACE ? &launch_trace<MsgT, NT, VPT, QL_DC, QL_DV> : nullptr;
+    k.decode_fn = (const void *)fused_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
+    k.launch_decode = &launch_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
+    if constexpr (TRACE) {
+        k.trace_fn = (const void *)fused_trace<MsgT, NT, VPT, QL_DC, QL_DV>;
+        k.launch_trace = &launch_trace<MsgT, NT, VPT, QL_DC, QL_DV>;
+    } else {
+        k.trace_fn = nullptr;
+        k.launch_trace = nullptr;
+    }
     return k;
 }
 
@@ -424,13 +513,15 @@ FusedKernel entry() {
 #endif
 
 void QL_EXPAND(QL_P, QL_DC, QL_DV)(const FusedKernel **out, int *n) {
-    // (threads, faults per thread): the smallest entry whose threads*vpt >= N is used;
-    // the last entry also serves the trace kernel.
+    // (threads, faults per thread, min resident blocks): the first entry whose
+    // threads * vpt >= N is used unless the caller asks for a block size; the last
+    // entry also serves the trace kernel.
     static const FusedKernel table[] = {
-        entry<256, 4, false>(),
-        entry<256, 12, false>(),
-        entry<512, 16, false>(),
-        entry<512, 32, true>(),
+        entry<256, 4, 4, false>(),
+        entry<512, 6, 2, false>(),
+        entry<256, 12, 3, false>(),
+        entry<512, 16, 1, false>(),
+        entry<512, 32, 1, true>(),
     };
     *out = table;
     *n = (int)(sizeof(table) / sizeof(table[0]));
