@@ -26,8 +26,10 @@
  *   - sign(x) = -1 iff x < 0, so sign(0) = +1; F_j = 1 iff Lambda_j < 0.
  *   - every message and marginal is clamped to [-clip, clip] after it is
  *     computed, and the minimum over an empty set is clip.
- *   - the weight of a solution is W = sum_j F_j w_j; a new solution replaces
- *     the kept one only if its weight is strictly lower.
+ *   - the weight of a solution is W = sum_j F_j w_j, compared exactly: the sum
+ *     is accumulated in double, which is exact for float32 w_j of magnitude
+ *     >= 2^-10 (and for w_j = 0) over up to 2^13 faults.  A new solution
+ *     replaces the kept one only if its weight is strictly lower.
  *   - convergence is tested after every iteration t >= 1; the iteration budget
  *     (max_total_iters > 0) is tested after the convergence test.
  *   - warm_mode 0 is the paper's chaining above; warm_mode 1 keeps
@@ -186,7 +188,7 @@ static void relay_one(const tanner *g, const REAL *w, const double *gamma_tab,
 
     int leg = 0, sols = 0, have = 0;
     int64_t iters = 0;
-    REAL best_w = 0;
+    double best_w = 0;
     for (;;) {
         int T = leg == 0 ? prm->T_first : prm->T_later;
         for (int j = 0; j < N; ++j) gbuf[j] = (REAL)gamma_tab[(size_t)leg * N + j];
@@ -194,8 +196,8 @@ static void relay_one(const tanner *g, const REAL *w, const double *gamma_tab,
             dmem_iteration(g, sigma, gbuf, prm->clip, s);
             iters++;
             if (syndrome_ok(g, sigma, s->F)) {
-                REAL W = 0;
-                for (int j = 0; j < N; ++j) if (s->F[j]) W += w[j];
+                double W = 0;
+                for (int j = 0; j < N; ++j) if (s->F[j]) W += (double)w[j];
                 if (!have || W < best_w) {
                     memcpy(s->best, s->F, (size_t)N);
                     best_w = W;
