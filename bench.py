@@ -200,7 +200,7 @@ def run_decode_only(args):
     syn = torch.from_numpy(pack_bits(sig).view(np.int64)).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    cfg = RelayConfig(stop_after_solutions=S_SOLUTIONS,
+    cfg = RelayConfig(stop_after_solutions=args.solutions,
                       msg_precision=QLDPC_MSG_FP16 if args.msg == "fp16" else QLDPC_MSG_FP32,
                       kernel=QLDPC_KERNEL_BASELINE if args.kernel == "baseline"
                       else QLDPC_KERNEL_FUSED, block_threads=args.block_threads)
@@ -210,6 +210,7 @@ def run_decode_only(args):
     iters = int(out[3].sum().item())
     ms = sum(times) / len(times)
     print(json.dumps({"mode": "decode-only", "kernel": args.kernel, "msg": args.msg,
+                      "S": args.solutions,
                       "shots": args.shots, "ms_per_step": ms,
                       "syndromes_per_s": args.shots / (ms / 1e3),
                       "iterations": iters, "block_threads": dec.info.block_threads,
@@ -376,9 +377,11 @@ def main():
     ap.add_argument("--kernel", choices=["fused", "baseline"], default="fused")
     ap.add_argument("--msg", choices=["fp32", "fp16"], default="fp32")
     ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--solutions", type=int, default=S_SOLUTIONS,
+                    help="S of a decode-only run")
     args = ap.parse_args()
     if (args.shots != SHOTS or args.kernel != "fused" or args.msg != "fp32"
-            or args.block_threads):
+            or args.block_threads or args.solutions != S_SOLUTIONS):
         args.only_decode = True
     if args.impl == "reference":
         run_reference(args)

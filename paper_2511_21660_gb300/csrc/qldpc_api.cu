@@ -175,28 +175,44 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
     g.syn_words = (M + 63) / 64;
     g.cor_words = (N + 63) / 64;
     g.f_words = 2 * g.cor_words + 2;
+    g.m_words = (M + 31) / 32;
+
+    // message layout (see FusedGraph): rows of DC slots, swizzled inside a row
+    const bool half = d->msg_fp16 != 0;
+    const int sh = DC >= 32 ? 0 : (DC == 16 ? 1 : 2);
+    auto swz = [&](int x) { return (x >> sh) & (DC - 1); };
+    auto byte_off = [&](int i, int k) {
+        return half ? (((i >> 1) * DC + (k ^ swz(i >> 1))) * 4 + (i & 1) * 2)
+                    : ((i * DC + (k ^ swz(i))) * 4);
+    };
+    const int msg_size = half ? 2 : 4;
+    g.msg_bytes = g.Mp * DC * msg_size;
+    if ((long long)g.Mp * DC * msg_size >= (1LL << 24))
+        return fail(QLDPC_ERR_UNSUPPORTED, "message array above 16 MB");
 
     std::vector<uint8_t> chk_deg(g.Mp, 0);
     std::vector<int> var_deg(N, 0);
-    std::vector<int32_t> chk_col((size_t)M * DC, N), var_slot((size_t)N * DV, 0);
-    std::vector<int32_t> slot_edge((size_t)DC * g.Mp, -1);
+    std::vector<int32_t> var_chk((size_t)N * DV, 0), var_slot((size_t)N * DV, 0);
+    std::vector<int32_t> slot_edge((size_t)g.Mp * DC, -1);
     std::vector<uint32_t> pad_mask((size_t)(g.Mp / 2) * DC, 0);
     for (int i = 0; i < M; ++i) {
         chk_deg[i] = (uint8_t)(row_ptr[i + 1] - row_ptr[i]);
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
             const int k = e - row_ptr[i], j = col_idx[e];
-            const int slot = k * g.Mp + i;
-            chk_col[(size_t)i * DC + k] = j;
-            slot_edge[slot] = e;
-            var_slot[(size_t)j * DV + var_deg[j]++] = slot;  // rows ascending => checks ascending
+            const int off = byte_off(i, k);
+            slot_edge[off / msg_size] = e;
+            var_chk[(size_t)j * DV + var_deg[j]] = i;
+            var_slot[(size_t)j * DV + var_deg[j]++] = off;  // rows ascending => checks ascending
         }
     }
     for (int j = 0; j < N; ++j) var_slot[(size_t)j * DV] |= var_deg[j] << 24;
     for (int i = 0; i < g.Mp; ++i)
-        for (int k = chk_deg[i]; k < DC; ++k)
-            pad_mask[(size_t)(i / 2) * DC + k] |= (i & 1) ? 0xffff0000u : 0x0000ffffu;
-    const int msg_bytes = d->msg_fp16 ? 2 : 4;
-    d->smem = fused_smem_bytes(g.Mp, DC, msg_bytes, g.f_words, g.syn_words);
+        for (int k = chk_deg[i]; k < DC; ++k) {
+            const int p = k ^ swz(i >> 1);
+            pad_mask[(size_t)(i / 2) * DC + p] |= (i & 1) ? 0xffff0000u : 0x0000ffffu;
+        }
+
+    d->smem = fused_smem_bytes(g.msg_bytes, g.f_words, g.syn_words, g.m_words, N);
     int optin = 0;
     QL_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device));
     QL_CUDA(cudaDeviceGetAttribute(&d->num_sms, cudaDevAttrMultiProcessorCount, d->device));
@@ -220,21 +236,21 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
     // one device arena for every graph array
     const size_t R1 = (size_t)d->prm.R + 1;
     size_t off[8], o = 0;
-    const size_t sizes[8] = {(size_t)g.Mp, sizeof(int32_t) * M * DC, sizeof(uint32_t) * pad_mask.size(),
+    const size_t sizes[8] = {(size_t)g.Mp, sizeof(int32_t) * N * DV, sizeof(uint32_t) * pad_mask.size(),
                              sizeof(int32_t) * N * DV, sizeof(float) * N, sizeof(float) * R1 * N,
-                             sizeof(int32_t) * DC * g.Mp, sizeof(unsigned int) * 4};
+                             sizeof(int32_t) * slot_edge.size(), sizeof(unsigned int) * 4};
     for (int q = 0; q < 8; ++q) {
         off[q] = o;
         o = align_up(o + sizes[q], 256);
     }
     QL_CUDA(cudaMalloc(&d->arena, o));
     char *base = static_cast<char *>(d->arena);
-    const void *src[7] = {chk_deg.data(), chk_col.data(), pad_mask.data(), var_slot.data(),
+    const void *src[7] = {chk_deg.data(), var_chk.data(), pad_mask.data(), var_slot.data(),
                           w.data(), gamma, slot_edge.data()};
     for (int q = 0; q < 7; ++q)
         QL_CUDA(cudaMemcpy(base + off[q], src[q], sizes[q], cudaMemcpyHostToDevice));
     g.chk_deg = reinterpret_cast<const uint8_t *>(base + off[0]);
-    g.chk_col = reinterpret_cast<const int32_t *>(base + off[1]);
+    g.var_chk = reinterpret_cast<const int32_t *>(base + off[1]);
     g.pad_mask = reinterpret_cast<const uint32_t *>(base + off[2]);
     g.var_slot = reinterpret_cast<const int32_t *>(base + off[3]);
     g.w = reinterpret_cast<const float *>(base + off[4]);

@@ -17,23 +17,28 @@ struct DevParams {
 };
 
 // Tanner graph in the layouts of the fused kernel.
-//   Slot (k, i) = k * Mp + i holds the message on the k-th edge of check i
-//   (edges of a check in increasing fault order); Mp = M rounded up to 32 so
-//   that a warp reading slot k of 32 consecutive checks hits 32 banks.
+//   The k-th edge of check i (edges of a check in increasing fault order) has its
+//   message at physical position p = k ^ swz(i) of the check's DC-slot row:
+//     float32:  element i*DC + p                      (byte offset 4 * element)
+//     binary16: checks 2q, 2q+1 share the 32-bit words q*DC + p, low half for even
+//               i (byte offset 4 * word + 2 * (i & 1)), swizzled by swz(q)
+//   with swz(x) = (x >> log2(32/DC)) & (DC-1).  Mp = M rounded up to 32.
 struct FusedGraph {
     int M, N, E, Mp;
+    int msg_bytes;        // bytes of the message array (Mp * DC * message size)
     int syn_words;        // ceil(M/64) uint64 words per syndrome
     int cor_words;        // ceil(N/64) uint64 words per correction
     int f_words;          // uint32 words of the decision bitmap (2*cor_words + 2)
+    int m_words;          // ceil(M/32) uint32 words of a parity bitmap
     const uint8_t *chk_deg;   // [Mp] check degrees (0 for rows M..Mp-1)
-    const int32_t *chk_col;   // [M][DC] fault of each slot, N for padding slots
-    const int32_t *var_slot;  // [N][DV] slots of the edges of fault j, increasing check
-                              // order; the top byte of entry 0 holds the fault degree
-    const uint32_t *pad_mask; // [Mp/2][DC] binary16 only: 0xffff in the half of the
-                              // check pair's word whose slot k is padding
+    const int32_t *var_chk;   // [N][DV] checks of fault j, increasing order
+    const int32_t *var_slot;  // [N][DV] byte offsets of the messages of fault j's edges,
+                              // increasing check order; top byte of entry 0 = degree
+    const uint32_t *pad_mask; // [Mp/2][DC] binary16 only: 0xffff in each half of the
+                              // pair's physical word p that holds a padding slot
     const float *w;           // [N] prior LLRs
     const float *gamma;       // [(R+1)][N]
-    const int32_t *slot_edge; // [DC*Mp] CSR edge id of each slot, -1 for padding (trace only)
+    const int32_t *slot_edge; // [Mp*DC] CSR edge id of each message element, -1 for padding
 };
 
 // CSR/CSC graph of the plain baseline kernel.
@@ -73,10 +78,10 @@ struct FusedKernel {
 };
 
 // Shared memory of the fused kernels for a graph (bytes).
-inline size_t fused_smem_bytes(int Mp, int dc, int msg_bytes, int f_words, int syn_words) {
-    size_t msg = (size_t)dc * Mp * msg_bytes;
-    msg = (msg + 15) & ~(size_t)15;
-    return msg + 4 * (size_t)f_words + 8 * (size_t)syn_words + 64;
+inline size_t fused_smem_bytes(int msg_bytes, int f_words, int syn_words, int m_words, int N) {
+    size_t msg = ((size_t)msg_bytes + 15) & ~(size_t)15;
+    return msg + 4 * (size_t)f_words + 8 * (size_t)syn_words + 8 * (size_t)m_words +
+           4 * (size_t)N + 64;
 }
 
 // Tables of compiled fused kernels, one per (precision, DC, DV) translation unit.

@@ -41,20 +41,24 @@ __device__ __forceinline__ BaseSmem base_layout(const BaseGraph &g, unsigned cha
     return s;
 }
 
-// Sum of w_j over the decided faults, in increasing j (warp 0, all lanes agree).
-__device__ float base_weight(const BaseGraph &g, const uint8_t *F) {
-    const int lane = threadIdx.x & 31;
-    float W = 0.0f;
-    for (int b0 = 0; b0 < g.N; b0 += 32) {
-        const int j = b0 + lane;
-        uint32_t bits = __ballot_sync(FULL, j < g.N && F[j]);
-        while (bits) {
-            const int l = __ffs(bits) - 1;
-            bits &= bits - 1;
-            W = __fadd_rn(W, g.w[b0 + l]);
-        }
-    }
-    return W;
+// Weight of a decided fault in 2^-33 units with integer operations only (exact
+// for float32 |w| >= 2^-10): |w| = m * 2^(e-23) -> m * 2^(e+10).
+__device__ __forceinline__ long long base_wfix(float w) {
+    const uint32_t b = __float_as_uint(w);
+    const int e = (int)((b >> 23) & 0xffu) - 127;
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    const long long a = e >= -10 ? (m << (e + 10)) : (e > -34 ? (m >> (-10 - e)) : 0ll);
+    return (b >> 31) ? -a : a;
+}
+
+// W = sum_j F_j w_j in 2^-33 units: per-warp partial sums into part[], added up by
+// every thread after a barrier (exact, independent of the order).
+__device__ void base_weight(const BaseGraph &g, const uint8_t *F, long long *part) {
+    long long s = 0;
+    for (int j = threadIdx.x; j < g.N; j += BASE_THREADS)
+        if (F[j]) s += base_wfix(g.w[j]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
 }
 
 __global__ void __launch_bounds__(BASE_THREADS) baseline_decode(BaseGraph g, DevParams p,
@@ -62,7 +66,7 @@ __global__ void __launch_bounds__(BASE_THREADS) baseline_decode(BaseGraph g, Dev
                                                                 DecodeOut out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BaseSmem s = base_layout(g, smem_raw);
-    __shared__ float s_W;
+    __shared__ long long s_Wpart[BASE_THREADS / 32];
     const int shot = blockIdx.x;
     const int tid = threadIdx.x;
     const float C = p.clip;
@@ -79,9 +83,8 @@ __global__ void __launch_bounds__(BASE_THREADS) baseline_decode(BaseGraph g, Dev
     __syncthreads();
 
     int leg = 0, sols = 0;
-    long long iters = 0;
+    long long iters = 0, Wbest = 0;
     bool have = false;
-    float Wbest = 0.0f;
     for (;;) {
         const int T = leg == 0 ? p.T1 : p.T2;
         const float *gam = g.gamma + (size_t)leg * g.N;
@@ -140,12 +143,10 @@ __global__ void __launch_bounds__(BASE_THREADS) baseline_decode(BaseGraph g, Dev
                 bad |= (int)par;
             }
             if (!__syncthreads_or(bad)) {
-                if (tid < 32) {
-                    const float W = base_weight(g, s.F);
-                    if (tid == 0) s_W = W;
-                }
+                base_weight(g, s.F, s_Wpart);
                 __syncthreads();
-                const float W = s_W;
+                long long W = 0;
+                for (int w = 0; w < BASE_THREADS / 32; ++w) W += s_Wpart[w];
                 if (!have || W < Wbest) {
                     for (int q = tid; q < g.cor_words; q += BASE_THREADS) {
                         uint64_t word = 0;

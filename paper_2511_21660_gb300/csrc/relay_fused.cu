@@ -3,15 +3,16 @@
 // One thread block decodes one syndrome at a time and pulls the next one from a
 // global work counter when it finishes (per-shot early exit, no idle blocks
 // behind slow shots).  Per shot:
-//   * the message of every edge lives in shared memory in one slot, overwritten
-//     in place: the check pass turns nu(t-1) into mu(t), the fault pass turns
-//     mu(t) into nu(t).  Slot (k, i) = k*Mp + i is the k-th edge of check i, so
-//     the check pass reads and writes whole warps of consecutive addresses and
-//     only the fault pass gathers;
+//   * every edge's message lives in shared memory in one slot, overwritten in
+//     place: the check pass turns nu(t-1) into mu(t), the fault pass turns mu(t)
+//     into nu(t).  The DC slots of a check are contiguous (128-bit loads and
+//     stores in the check pass), with their order inside the check XOR-swizzled
+//     by the check index so that the fault pass's gathers and scatters over
+//     consecutive checks fall into distinct banks;
 //   * the per-fault state (Lambda_j, (1-gamma_j) lambda_j(0), gamma_j) lives in
 //     registers: fault j belongs to thread j mod NT for the whole shot;
-//   * decisions F_j = [Lambda_j < 0] are packed by warp ballots into a bitmap in
-//     shared memory, and H F = sigma is tested by XOR over each check's slots.
+//   * decisions F_j = [Lambda_j < 0] are packed by warp ballots into a bitmap, and
+//     the syndrome H F is accumulated by the (few) faults with F_j = 1.
 // All float arithmetic rounds every + and * separately (__fadd_rn/__fmul_rn), in
 // the same order as the single-precision oracle, so results are bit-identical.
 //
@@ -40,19 +41,46 @@ template <typename MT>
 struct Msg;
 template <>
 struct Msg<float> {
-    static __device__ __forceinline__ float ld(const float *p) { return *p; }
-    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ float ld(const unsigned char *base, int off) {
+        return *reinterpret_cast<const float *>(base + off);
+    }
+    static __device__ __forceinline__ void st(unsigned char *base, int off, float v) {
+        *reinterpret_cast<float *>(base + off) = v;
+    }
 };
 template <>
 struct Msg<__half> {
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
-    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float ld(const unsigned char *base, int off) {
+        return __half2float(*reinterpret_cast<const __half *>(base + off));
+    }
+    static __device__ __forceinline__ void st(unsigned char *base, int off, float v) {
+        *reinterpret_cast<__half *>(base + off) = __float2half_rn(v);
+    }
 };
 
 __device__ __forceinline__ float clampc(float x, float c) { return fminf(fmaxf(x, -c), c); }
 
-// Per-fault edge list: DV slot indices, the first one carrying the fault degree
-// in its top byte (slot indices are below 2^24).
+// x + 0 = x for x != 0 and -0 + 0 = +0.  Applied to lambda(0) and to
+// (1 - gamma) lambda(0) at the start of a leg, it guarantees that lambda(t) and
+// therefore every stored message nu (a sum starting from lambda(t)) is never -0,
+// so the check pass may read sign(nu) = -1 iff nu < 0 straight off the sign bit.
+// A zero's sign never changes a comparison or a non-zero result, so this leaves
+// every decision and every non-zero value as in the oracle.
+__device__ __forceinline__ float canon(float x) { return __fadd_rn(x, 0.0f); }
+
+// Weight of a decided fault in 2^-33 units, from the float's fields with integer
+// operations only: |w| = m * 2^(e-23) -> m * 2^(e+10).  Exact for |w| >= 2^-10
+// (smaller magnitudes are truncated); |w| < 2^20 keeps it below 2^54.
+__device__ __forceinline__ long long wfix(float w) {
+    const uint32_t b = __float_as_uint(w);
+    const int e = (int)((b >> 23) & 0xffu) - 127;
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    const long long a = e >= -10 ? (m << (e + 10)) : (e > -34 ? (m >> (-10 - e)) : 0ll);
+    return (b >> 31) ? -a : a;
+}
+
+// Per-fault edge list: DV byte offsets of the fault's slots (increasing check
+// order); entry 0 carries the fault degree in its top byte.
 template <int DV>
 __device__ __forceinline__ int load_slots(const FusedGraph &g, int j, int (&sl)[DV]) {
     const int4 *p = reinterpret_cast<const int4 *>(g.var_slot + (size_t)j * DV);
@@ -77,10 +105,14 @@ __device__ __forceinline__ int load_slots(const FusedGraph &g, int j, int (&sl)[
     return deg;
 }
 
-// Messages are stored with zeros canonicalised to +0 (x + 0 = x for x != 0 and
-// -0 + 0 = +0), so that the check pass may take the sign of a stored message from
-// its sign bit: sign(x) = -1 iff x < 0 then holds bit for bit.
-__device__ __forceinline__ float canon(float x) { return __fadd_rn(x, 0.0f); }
+// Swizzle of the slots inside a check (or check pair): physical position p holds
+// logical slot p ^ swz(i); with 32/DC checks per 128-byte row, this spreads a
+// fixed logical slot of 32 consecutive rows over 32 banks.
+template <int DC>
+__device__ __forceinline__ int swz(int i) {
+    constexpr int sh = DC >= 32 ? 0 : (DC == 16 ? 1 : 2);
+    return (i >> sh) & (DC - 1);
+}
 
 // Start of a leg: lambda(0), Lambda(0), nu(0) and the leg's memory strengths.
 //   leg 0:  lambda(0) = Lambda(0) = w
@@ -89,24 +121,24 @@ __device__ __forceinline__ float canon(float x) { return __fadd_rn(x, 0.0f); }
 // bb holds (1 - gamma_j) * lambda_j(0), rounded, which is the first product of
 // the memory update and is constant within a leg.
 template <typename MT, int NT, int VPT, int DV>
-__device__ __forceinline__ void leg_init(const FusedGraph &g, const DevParams &p, int leg, MT *msg,
-                                         float (&Lam)[VPT], float (&bb)[VPT], float (&gg)[VPT]) {
+__device__ __forceinline__ void leg_init(const FusedGraph &g, const DevParams &p, int leg,
+                                         unsigned char *msg, const float *ws, float (&Lam)[VPT],
+                                         float (&bb)[VPT], float (&gg)[VPT]) {
     const float *grow = g.gamma + (size_t)leg * g.N;
 #pragma unroll
     for (int r = 0; r < VPT; ++r) {
         const int j = threadIdx.x + r * NT;
         if (j < g.N) {
-            const float lam0 = (leg == 0 || p.warm_mode == 1) ? __ldg(g.w + j) : Lam[r];
+            const float lam0 = canon((leg == 0 || p.warm_mode == 1) ? ws[j] : Lam[r]);
             if (leg == 0) Lam[r] = lam0;
             const float gm = __ldg(grow + j);
             gg[r] = gm;
-            bb[r] = __fmul_rn(__fsub_rn(1.0f, gm), lam0);
+            bb[r] = canon(__fmul_rn(__fsub_rn(1.0f, gm), lam0));
             int sl[DV];
             const int deg = load_slots<DV>(g, j, sl);
-            const float nu0 = canon(lam0);
 #pragma unroll
             for (int k = 0; k < DV; ++k)
-                if (k < deg) Msg<MT>::st(msg + sl[k], nu0);
+                if (k < deg) Msg<MT>::st(msg, sl[k], lam0);
         }
     }
 }
@@ -114,17 +146,26 @@ __device__ __forceinline__ void leg_init(const FusedGraph &g, const DevParams &p
 // Check pass, float32 messages: mu_{i->j}(t) from nu(t-1) for every check, in place.
 // (m1, m2) = the two smallest magnitudes of the check's slots (with multiplicity),
 // so the min over the excluded set of slot k is m2 if |nu_k| = m1, else m1.
-// Padding slots hold C, which is also the min over an empty set, and are never
-// written.  The sign is (-1)^sigma_i times the product of all signs times sign(nu_k).
+// Padding slots hold C, which is also the min over an empty set, and keep it.
+// The sign is (-1)^sigma_i times the product of all signs times sign(nu_k).
+// Slots are processed in physical order: the rule does not depend on the order.
 template <int NT, int DC>
 __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, const uint32_t *sg,
-                                           float C) {
+                                           uint32_t *par_zero, float C) {
+    for (int q = threadIdx.x; q < g.m_words; q += NT) par_zero[q] = 0u;
     for (int i = threadIdx.x; i < g.M; i += NT) {
         const int deg = g.chk_deg[i];
         uint32_t sx = sg[i >> 5] << (31 - (i & 31));
+        float4 *row = reinterpret_cast<float4 *>(msg + (size_t)i * DC);
         float v[DC];
 #pragma unroll
-        for (int k = 0; k < DC; ++k) v[k] = msg[k * g.Mp + i];
+        for (int k4 = 0; k4 < DC / 4; ++k4) {
+            const float4 t = row[k4];
+            v[4 * k4] = t.x;
+            v[4 * k4 + 1] = t.y;
+            v[4 * k4 + 2] = t.z;
+            v[4 * k4 + 3] = t.w;
+        }
         float m1 = C, m2 = C;
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
@@ -134,34 +175,50 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, cons
             sx ^= __float_as_uint(v[k]);
         }
         sx &= 0x80000000u;
+        float o[DC];
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
-            if (k < deg) {
-                const float mag = (fabsf(v[k]) <= m1) ? m2 : m1;
-                msg[k * g.Mp + i] = __uint_as_float(__float_as_uint(mag) |
-                                                    ((sx ^ __float_as_uint(v[k])) & 0x80000000u));
-            }
+            const float mag = (fabsf(v[k]) <= m1) ? m2 : m1;
+            o[k] = __uint_as_float(__float_as_uint(mag) |
+                                   ((sx ^ __float_as_uint(v[k])) & 0x80000000u));
         }
+        if (deg < DC) {
+            const int f = swz<DC>(i);
+#pragma unroll
+            for (int k = 0; k < DC; ++k)
+                if ((k ^ f) >= deg) o[k] = C;
+        }
+#pragma unroll
+        for (int k4 = 0; k4 < DC / 4; ++k4)
+            row[k4] = make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
     }
 }
 
-// Check pass, binary16 messages: two checks (2q, 2q+1) per thread with half2
-// arithmetic (min, max and sign manipulation are exact in any format).  A 32-bit
-// word of slot k holds both checks; a per-pair mask keeps C in padding lanes.
+// Check pass, binary16 messages: checks 2q and 2q+1 share each 32-bit word (low
+// and high half), processed together with half2 arithmetic; min, max and sign
+// manipulation are exact in any format.  A per-pair mask keeps C in padding halves.
 template <int NT, int DC>
 __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, const uint32_t *sg,
-                                           float C) {
-    uint32_t *w32 = reinterpret_cast<uint32_t *>(msg);
-    const int Mp2 = g.Mp >> 1, M2 = (g.M + 1) >> 1;
+                                           uint32_t *par_zero, float C) {
+    for (int q = threadIdx.x; q < g.m_words; q += NT) par_zero[q] = 0u;
     const __half2 C2 = __float2half2_rn(C);
     const uint32_t c2 = *reinterpret_cast<const uint32_t *>(&C2);
+    const int M2 = (g.M + 1) >> 1;
     for (int q = threadIdx.x; q < M2; q += NT) {
         const int i = 2 * q;
         const uint32_t sb = (sg[i >> 5] >> (i & 31)) & 3u;
         uint32_t sx = ((sb & 1u) << 15) | ((sb & 2u) << 30);
+        const bool full = g.chk_deg[i] == DC && g.chk_deg[i + 1] == DC;
+        uint4 *row = reinterpret_cast<uint4 *>(msg + (size_t)q * 2 * DC);
         uint32_t v[DC];
 #pragma unroll
-        for (int k = 0; k < DC; ++k) v[k] = w32[k * Mp2 + q];
+        for (int k4 = 0; k4 < DC / 4; ++k4) {
+            const uint4 t = row[k4];
+            v[4 * k4] = t.x;
+            v[4 * k4 + 1] = t.y;
+            v[4 * k4 + 2] = t.z;
+            v[4 * k4 + 3] = t.w;
+        }
         __half2 m1 = C2, m2 = C2;
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
@@ -173,51 +230,54 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, con
         sx &= 0x80008000u;
         const uint32_t u1 = *reinterpret_cast<const uint32_t *>(&m1);
         const uint32_t u2 = *reinterpret_cast<const uint32_t *>(&m2);
-        const uint4 *pm4 = reinterpret_cast<const uint4 *>(g.pad_mask + (size_t)q * DC);
-        uint32_t pm[DC];
-#pragma unroll
-        for (int k4 = 0; k4 < DC / 4; ++k4) {
-            const uint4 t = __ldg(pm4 + k4);
-            pm[4 * k4] = t.x;
-            pm[4 * k4 + 1] = t.y;
-            pm[4 * k4 + 2] = t.z;
-            pm[4 * k4 + 3] = t.w;
-        }
+        uint32_t o[DC];
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
             const __half2 a = __habs2(*reinterpret_cast<const __half2 *>(&v[k]));
             const uint32_t eq = __hle2_mask(a, m1);
-            const uint32_t mag = (u2 & eq) | (u1 & ~eq);
-            const uint32_t o = mag | ((sx ^ v[k]) & 0x80008000u);
-            w32[k * Mp2 + q] = (o & ~pm[k]) | (c2 & pm[k]);
+            o[k] = ((u2 & eq) | (u1 & ~eq)) | ((sx ^ v[k]) & 0x80008000u);
         }
+        if (!full) {
+            const uint4 *pm4 = reinterpret_cast<const uint4 *>(g.pad_mask + (size_t)q * DC);
+#pragma unroll
+            for (int k4 = 0; k4 < DC / 4; ++k4) {
+                const uint4 t = __ldg(pm4 + k4);
+                o[4 * k4] = (o[4 * k4] & ~t.x) | (c2 & t.x);
+                o[4 * k4 + 1] = (o[4 * k4 + 1] & ~t.y) | (c2 & t.y);
+                o[4 * k4 + 2] = (o[4 * k4 + 2] & ~t.z) | (c2 & t.z);
+                o[4 * k4 + 3] = (o[4 * k4 + 3] & ~t.w) | (c2 & t.w);
+            }
+        }
+#pragma unroll
+        for (int k4 = 0; k4 < DC / 4; ++k4)
+            row[k4] = make_uint4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
     }
 }
 
 // Fault update for one fault: memory term, marginal, excluded sums (increasing check
 // order, one rounding per addition, exactly as written in the oracle).
 template <typename MT, int DV>
-__device__ __forceinline__ float fault_update(MT *msg, const int (&sl)[DV], int deg, float lam,
-                                              float C) {
+__device__ __forceinline__ float fault_update(unsigned char *msg, const int (&sl)[DV], int deg,
+                                              float lam, float C) {
     if (deg == 3) {
-        const float mu0 = Msg<MT>::ld(msg + sl[0]), mu1 = Msg<MT>::ld(msg + sl[1]),
-                    mu2 = Msg<MT>::ld(msg + sl[2]);
+        const float mu0 = Msg<MT>::ld(msg, sl[0]), mu1 = Msg<MT>::ld(msg, sl[1]),
+                    mu2 = Msg<MT>::ld(msg, sl[2]);
         const float s0 = __fadd_rn(lam, mu0), s01 = __fadd_rn(s0, mu1);
-        Msg<MT>::st(msg + sl[0], canon(clampc(__fadd_rn(__fadd_rn(lam, mu1), mu2), C)));
-        Msg<MT>::st(msg + sl[1], canon(clampc(__fadd_rn(s0, mu2), C)));
-        Msg<MT>::st(msg + sl[2], canon(clampc(s01, C)));
+        Msg<MT>::st(msg, sl[0], clampc(__fadd_rn(__fadd_rn(lam, mu1), mu2), C));
+        Msg<MT>::st(msg, sl[1], clampc(__fadd_rn(s0, mu2), C));
+        Msg<MT>::st(msg, sl[2], clampc(s01, C));
         return clampc(__fadd_rn(s01, mu2), C);
     }
     if (deg == 2) {
-        const float mu0 = Msg<MT>::ld(msg + sl[0]), mu1 = Msg<MT>::ld(msg + sl[1]);
+        const float mu0 = Msg<MT>::ld(msg, sl[0]), mu1 = Msg<MT>::ld(msg, sl[1]);
         const float s0 = __fadd_rn(lam, mu0);
-        Msg<MT>::st(msg + sl[0], canon(clampc(__fadd_rn(lam, mu1), C)));
-        Msg<MT>::st(msg + sl[1], canon(clampc(s0, C)));
+        Msg<MT>::st(msg, sl[0], clampc(__fadd_rn(lam, mu1), C));
+        Msg<MT>::st(msg, sl[1], clampc(s0, C));
         return clampc(__fadd_rn(s0, mu1), C);
     }
     float mu[DV];
 #pragma unroll
-    for (int k = 0; k < DV; ++k) mu[k] = (k < deg) ? Msg<MT>::ld(msg + sl[k]) : 0.0f;
+    for (int k = 0; k < DV; ++k) mu[k] = (k < deg) ? Msg<MT>::ld(msg, sl[k]) : 0.0f;
     float L = lam;
 #pragma unroll
     for (int k = 0; k < DV; ++k)
@@ -229,17 +289,21 @@ __device__ __forceinline__ float fault_update(MT *msg, const int (&sl)[DV], int 
 #pragma unroll
             for (int k2 = 0; k2 < DV; ++k2)
                 if (k2 != k && k2 < deg) v = __fadd_rn(v, mu[k2]);
-            Msg<MT>::st(msg + sl[k], canon(clampc(v, C)));
+            Msg<MT>::st(msg, sl[k], clampc(v, C));
         }
     }
     return clampc(L, C);
 }
 
-// Fault pass: memory update, marginals, fault->check messages, decisions into the bitmap.
+// Fault pass: memory update, marginals, fault->check messages, decisions into the
+// bitmap fw, and the syndrome of the decision: every fault with F_j = 1 flips the
+// parity bits of its checks in par (zeroed by the preceding check pass).  Decisions
+// are sparse, so this costs a few atomics per shot instead of a pass over all edges.
 template <typename MT, int NT, int VPT, int DV>
-__device__ __forceinline__ void fault_pass(const FusedGraph &g, MT *msg, uint32_t *fw,
-                                           float (&Lam)[VPT], const float (&bb)[VPT],
-                                           const float (&gg)[VPT], float C) {
+__device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *msg, uint32_t *fw,
+                                           uint32_t *par, float (&Lam)[VPT],
+                                           const float (&bb)[VPT], const float (&gg)[VPT],
+                                           float C) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int r = 0; r < VPT; ++r) {
@@ -252,6 +316,13 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, MT *msg, uint32_
             const int deg = load_slots<DV>(g, j, sl);
             L = fault_update<MT, DV>(msg, sl, deg, lam, C);
             Lam[r] = L;
+            if (L < 0.0f) {
+                const int *ck = g.var_chk + (size_t)j * DV;
+                for (int k = 0; k < deg; ++k) {
+                    const int c = __ldg(ck + k);
+                    atomicXor(par + (c >> 5), 1u << (c & 31));
+                }
+            }
         }
         const uint32_t bal = __ballot_sync(FULL, valid && L < 0.0f);
         const int jb = threadIdx.x - lane + r * NT;
@@ -259,48 +330,37 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, MT *msg, uint32_
     }
 }
 
-// H F = sigma ?  Returns true (in every thread) when some check is unsatisfied.
-// Padding slots name fault N, whose decision bit is always 0.
-template <int NT, int DC>
-__device__ __forceinline__ bool syndrome_unsat(const FusedGraph &g, const uint32_t *fw,
-                                               const uint32_t *sg) {
+// H F = sigma ?  Each warp compares the parity words with the syndrome on its own
+// (no block barrier); every warp reaches the same answer.
+__device__ __forceinline__ bool warp_converged(const uint32_t *par, const uint32_t *sg, int nw) {
     uint32_t bad = 0;
-    for (int i = threadIdx.x; i < g.M; i += NT) {
-        uint32_t par = sg[i >> 5] >> (i & 31);
-        const int4 *c4 = reinterpret_cast<const int4 *>(g.chk_col + (size_t)i * DC);
-#pragma unroll
-        for (int q = 0; q < DC / 4; ++q) {
-            const int4 c = __ldg(c4 + q);
-            const uint32_t wx = fw[c.x >> 5], wy = fw[c.y >> 5], wz = fw[c.z >> 5],
-                           ww = fw[c.w >> 5];
-            par ^= __funnelshift_r(wx, wx, c.x) ^ __funnelshift_r(wy, wy, c.y) ^
-                   __funnelshift_r(wz, wz, c.z) ^ __funnelshift_r(ww, ww, c.w);
-        }
-        bad |= par & 1u;
-    }
-    return __syncthreads_or(bad) != 0;
+    for (int q = threadIdx.x & 31; q < nw; q += 32) bad |= par[q] ^ sg[q];
+    return !__any_sync(FULL, bad != 0u);
 }
 
-// W = sum_j F_j w_j in increasing j, one rounding per addition (called by one
-// whole warp; every lane returns the same value).
-__device__ __forceinline__ float solution_weight(const FusedGraph &g, const uint32_t *fw) {
-    const int lane = threadIdx.x & 31;
-    const int nw = (g.N + 31) >> 5;
-    float W = 0.0f;
-    for (int q0 = 0; q0 < nw; q0 += 32) {
-        const uint32_t mine = (q0 + lane < nw) ? fw[q0 + lane] : 0u;
-        uint32_t any = __ballot_sync(FULL, mine != 0u);
-        while (any) {
-            const int l = __ffs(any) - 1;
-            any &= any - 1;
-            uint32_t wd = __shfl_sync(FULL, mine, l);
-            while (wd) {
-                const int b = __ffs(wd) - 1;
-                wd &= wd - 1;
-                W = __fadd_rn(W, __ldg(g.w + ((q0 + l) << 5) + b));
-            }
-        }
+// This thread's share of the solution weight sum_j F_j w_j (2^-33 units), reduced
+// over the warp; lane 0 stores the warp's partial in part[warp].  After a barrier
+// every thread adds the NT/32 partials: integer addition makes the total exact and
+// independent of the order.
+template <int NT, int VPT>
+__device__ __forceinline__ void warp_weight(const FusedGraph &g, const float *ws,
+                                            const float (&Lam)[VPT], long long *part) {
+    long long s = 0;
+#pragma unroll
+    for (int r = 0; r < VPT; ++r) {
+        const int j = threadIdx.x + r * NT;
+        if (j < g.N && Lam[r] < 0.0f) s += wfix(ws[j]);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+}
+
+template <int NT>
+__device__ __forceinline__ long long total_weight(const long long *part) {
+    long long W = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) W += part[w];
     return W;
 }
 
@@ -310,21 +370,34 @@ __device__ __forceinline__ void store_bits(uint64_t *dst, const uint32_t *fw, in
         dst[q] = (uint64_t)fw[2 * q] | ((uint64_t)fw[2 * q + 1] << 32);
 }
 
-template <typename MT, int DC>
-__device__ __forceinline__ void smem_layout(const FusedGraph &g, unsigned char *raw, MT *&msg,
-                                            uint32_t *&fw, uint32_t *&sg) {
-    msg = reinterpret_cast<MT *>(raw);
-    const size_t mb = ((size_t)DC * g.Mp * sizeof(MT) + 15) & ~(size_t)15;
+// Shared memory: messages [msg_bytes], decision bitmap fw [f_words], syndrome sg
+// [2*syn_words] (bits past M cleared), two parity buffers par [2][m_words], prior
+// LLRs ws [N] (read by the weight sum and by leg initialisation).
+__device__ __forceinline__ void smem_layout(const FusedGraph &g, unsigned char *raw,
+                                            uint32_t *&fw, uint32_t *&sg, uint32_t *&par,
+                                            float *&ws) {
+    const size_t mb = ((size_t)g.msg_bytes + 15) & ~(size_t)15;
     fw = reinterpret_cast<uint32_t *>(raw + mb);
     sg = fw + g.f_words;
+    par = sg + 2 * g.syn_words;
+    ws = reinterpret_cast<float *>(par + 2 * g.m_words);
 }
 
+// Padding slots of every check hold C for good (the check pass writes C back).
 template <typename MT, int NT, int DC>
-__device__ __forceinline__ void block_setup(const FusedGraph &g, MT *msg, uint32_t *fw, float C) {
+__device__ __forceinline__ void block_setup(const FusedGraph &g, unsigned char *msg, uint32_t *fw,
+                                            float *ws, float C) {
     for (int q = threadIdx.x; q < g.f_words; q += NT) fw[q] = 0u;
+    for (int j = threadIdx.x; j < g.N; j += NT) ws[j] = __ldg(g.w + j);
     for (int i = threadIdx.x; i < g.Mp; i += NT) {
         const int deg = g.chk_deg[i];
-        for (int k = deg; k < DC; ++k) Msg<MT>::st(msg + k * g.Mp + i, C);
+        const bool half = sizeof(MT) == 2;
+        const int f = half ? swz<DC>(i >> 1) : swz<DC>(i);
+        for (int k = deg; k < DC; ++k) {
+            const int p = k ^ f;
+            const int off = half ? (((i >> 1) * DC + p) * 4 + (i & 1) * 2) : ((i * DC + p) * 4);
+            Msg<MT>::st(msg, off, C);
+        }
     }
 }
 
@@ -332,25 +405,31 @@ template <int NT>
 __device__ __forceinline__ void load_syndrome(const FusedGraph &g, const uint64_t *sy,
                                               uint32_t *sg) {
     for (int q = threadIdx.x; q < g.syn_words; q += NT) {
-        const uint64_t v = __ldg(sy + q);
+        uint64_t v = __ldg(sy + q);
+        const int hi = g.M - 64 * q;  // padding bits of the last word are ignored
+        if (hi < 64) v &= (1ull << hi) - 1ull;
         sg[2 * q] = (uint32_t)v;
         sg[2 * q + 1] = (uint32_t)(v >> 32);
     }
 }
 
+// One block per shot at a time; shots come from a global counter.  Per iteration:
+// check pass | barrier | fault pass | barrier | per-warp convergence test.  A leg
+// end adds the weight reduction, the next leg's initialisation and one barrier.
 template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
 __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams p,
                                                    const uint64_t *__restrict__ syn, int B,
                                                    DecodeOut out, unsigned int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    MT *msg;
-    uint32_t *fw, *sg;
-    smem_layout<MT, DC>(g, smem_raw, msg, fw, sg);
+    unsigned char *msg = smem_raw;
+    uint32_t *fw, *sg, *par;
+    float *ws;
+    smem_layout(g, smem_raw, fw, sg, par, ws);
     __shared__ int s_shot;
-    __shared__ float s_W;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ long long s_Wpart[NT / 32];
+    const int tid = threadIdx.x;
     const float C = p.clip;
-    block_setup<MT, NT, DC>(g, msg, fw, C);
+    block_setup<MT, NT, DC>(g, msg, fw, ws, C);
 
     float Lam[VPT], bb[VPT], gg[VPT];
 #pragma unroll
@@ -365,42 +444,44 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
         load_syndrome<NT>(g, syn + (size_t)shot * g.syn_words, sg);
         uint64_t *cor = out.corr + (size_t)shot * g.cor_words;
 
-        int leg = 0, sols = 0;
-        long long iters = 0;
+        int leg = 0, sols = 0, t = 0, pb = 0;
+        long long iters = 0, Wbest = 0;
         bool have = false;
-        float Wbest = 0.0f;
-        leg_init<MT, NT, VPT, DV>(g, p, 0, msg, Lam, bb, gg);
+        leg_init<MT, NT, VPT, DV>(g, p, 0, msg, ws, Lam, bb, gg);
         __syncthreads();
         for (;;) {
-            const int T = leg == 0 ? p.T1 : p.T2;
-            for (int t = 1; t <= T; ++t) {
-                check_pass<NT, DC>(g, msg, sg, C);
-                __syncthreads();
-                fault_pass<MT, NT, VPT, DV>(g, msg, fw, Lam, bb, gg, C);
-                __syncthreads();
-                ++iters;
-                if (!syndrome_unsat<NT, DC>(g, fw, sg)) {
-                    if (warp == 0) {
-                        const float W = solution_weight(g, fw);
-                        if (lane == 0) s_W = W;
-                    }
-                    __syncthreads();
-                    const float W = s_W;
-                    if (!have || W < Wbest) {
-                        store_bits<NT>(cor, fw, g.cor_words);
-                        have = true;
-                        Wbest = W;
-                    }
-                    ++sols;
-                    break;
-                }
-                if (p.max_iters > 0 && iters >= p.max_iters) break;
-            }
-            const bool spent = p.max_iters > 0 && iters >= p.max_iters;
-            if (sols >= p.S || leg == p.R || spent) break;
-            ++leg;
-            leg_init<MT, NT, VPT, DV>(g, p, leg, msg, Lam, bb, gg);
+            uint32_t *pc = par + pb * g.m_words;
+            check_pass<NT, DC>(g, reinterpret_cast<MT *>(msg), sg, pc, C);
             __syncthreads();
+            fault_pass<MT, NT, VPT, DV>(g, msg, fw, pc, Lam, bb, gg, C);
+            __syncthreads();
+            ++iters;
+            ++t;
+            pb ^= 1;
+            const bool conv = warp_converged(pc, sg, g.m_words);
+            const bool spent = p.max_iters > 0 && iters >= p.max_iters;
+            const bool leg_end = conv || spent || t == (leg == 0 ? p.T1 : p.T2);
+            if (!leg_end) continue;
+            if (conv) {
+                ++sols;
+                warp_weight<NT, VPT>(g, ws, Lam, s_Wpart);
+            }
+            const bool done = sols >= p.S || leg == p.R || spent;
+            if (!done) {
+                ++leg;
+                t = 0;
+                leg_init<MT, NT, VPT, DV>(g, p, leg, msg, ws, Lam, bb, gg);
+            }
+            __syncthreads();  // the weight and the next leg's initial messages are visible
+            if (conv) {
+                const long long W = total_weight<NT>(s_Wpart);
+                if (!have || W < Wbest) {
+                    store_bits<NT>(cor, fw, g.cor_words);
+                    have = true;
+                    Wbest = W;
+                }
+            }
+            if (done) break;
         }
         if (!have) store_bits<NT>(cor, fw, g.cor_words);
         if (tid == 0) {
@@ -417,31 +498,32 @@ __global__ void __launch_bounds__(NT) fused_trace(FusedGraph g, DevParams p,
                                                   const uint64_t *__restrict__ syn, int B, int T,
                                                   int E, float *marg, float *nu, float *mu) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    MT *msg;
-    uint32_t *fw, *sg;
-    smem_layout<MT, DC>(g, smem_raw, msg, fw, sg);
+    unsigned char *msg = smem_raw;
+    uint32_t *fw, *sg, *par;
+    float *ws;
+    smem_layout(g, smem_raw, fw, sg, par, ws);
     const int shot = blockIdx.x;
     const float C = p.clip;
-    block_setup<MT, NT, DC>(g, msg, fw, C);
+    block_setup<MT, NT, DC>(g, msg, fw, ws, C);
     load_syndrome<NT>(g, syn + (size_t)shot * g.syn_words, sg);
     float Lam[VPT], bb[VPT], gg[VPT];
 #pragma unroll
     for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
     __syncthreads();
-    leg_init<MT, NT, VPT, DV>(g, p, 0, msg, Lam, bb, gg);
+    leg_init<MT, NT, VPT, DV>(g, p, 0, msg, ws, Lam, bb, gg);
     __syncthreads();
-    const int nslots = DC * g.Mp;
+    const int nslots = g.msg_bytes / (int)sizeof(MT);
     for (int t = 0; t < T; ++t) {
         const size_t o = (size_t)t * B + shot;
-        check_pass<NT, DC>(g, msg, sg, C);
+        check_pass<NT, DC>(g, reinterpret_cast<MT *>(msg), sg, par, C);
         __syncthreads();
         if (mu)
             for (int s = threadIdx.x; s < nslots; s += NT) {
                 const int e = g.slot_edge[s];
-                if (e >= 0) mu[o * E + e] = Msg<MT>::ld(msg + s);
+                if (e >= 0) mu[o * E + e] = Msg<MT>::ld(msg, s * (int)sizeof(MT));
             }
         __syncthreads();
-        fault_pass<MT, NT, VPT, DV>(g, msg, fw, Lam, bb, gg, C);
+        fault_pass<MT, NT, VPT, DV>(g, msg, fw, par, Lam, bb, gg, C);
         __syncthreads();
         if (marg) {
 #pragma unroll
@@ -453,7 +535,7 @@ __global__ void __launch_bounds__(NT) fused_trace(FusedGraph g, DevParams p,
         if (nu)
             for (int s = threadIdx.x; s < nslots; s += NT) {
                 const int e = g.slot_edge[s];
-                if (e >= 0) nu[o * E + e] = Msg<MT>::ld(msg + s);
+                if (e >= 0) nu[o * E + e] = Msg<MT>::ld(msg, s * (int)sizeof(MT));
             }
         __syncthreads();
     }
