@@ -125,6 +125,32 @@ int qldpc_decode_batch_host(qldpc_decoder *d, const uint64_t *syndromes, int64_t
                             int32_t *iters);
 
 /*
+ * Size of the static scratch area used by qldpc_decode_batch_host_static: 8 MiB of
+ * device memory that every GPU loading this library holds until the process exits.
+ */
+#define QLDPC_STATIC_SCRATCH_BYTES (8 * 1024 * 1024)
+
+/*
+ * qldpc_decode_batch_host with no allocation at all.  (The paper has no
+ * counterpart: this serves callers that cannot allocate device memory while they
+ * decode, such as a real-time loop with a fixed memory budget or a process whose
+ * device memory is owned by another allocator; qldpc_decode_batch_host allocates
+ * its staging buffers on first use and whenever the batch grows.)
+ * The syndromes, outputs and the kernel's work counter are staged in one static
+ * device array of QLDPC_STATIC_SCRATCH_BYTES; a batch must fit in it (for the gross
+ * code, 936 x 2736, about 17,000 shots per call), else INVALID_ARG names the limit.
+ * Host pointers as in qldpc_decode_batch_host; synchronous on the handle's internal
+ * stream.  The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call on a device
+ * shares the one array, which keeps the previous call's contents (the work counter
+ * is cleared by each call): calls that overlap on the GPU, from any handle, race.
+ * Fused kernel only (UNSUPPORTED for the baseline kernel).
+ */
+int qldpc_decode_batch_host_static(qldpc_decoder *d, const uint64_t *syndromes, int64_t B,
+                                   uint64_t *corrections, int32_t *legs_used,
+                                   uint8_t *converged, int32_t *iters);
+
+/*
  * Run T iterations of the first leg (memory strengths = row 0 of the gamma table)
  * on B syndromes with no early exit, recording every iteration, for checking
  * message precision.  Outputs (device, float32, may be NULL):

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -449,6 +450,94 @@ int qldpc_decode_batch_host(qldpc_decoder *d, const uint64_t *syndromes, int64_t
     QL_CUDA(cudaStreamSynchronize(st));
     return QLDPC_OK;
 }
+
+}  // extern "C"
+
+// ---- host-buffer decode without any allocation ------------------------------------
+//
+// qldpc_decode_batch_host stages batches in device buffers that it allocates on
+// first use and whenever a batch is larger than any before.  Callers that must not
+// allocate device memory while decoding (a real-time loop with a fixed memory
+// budget, a process whose device memory belongs to another allocator) use
+// qldpc_decode_batch_host_static instead: its staging area and the fused kernel's
+// work counter live in the file-scope array below, which every GPU that loads the
+// library holds until the process exits.
+
+static __device__ __align__(256) unsigned char g_static_scratch[QLDPC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void *g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up once per
+// device; the host-side symbol is only a stand-in and must not reach a kernel).
+int static_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= kMaxDevices)
+        return fail(QLDPC_ERR_UNSUPPORTED, "device ordinal %d above %d", device, kMaxDevices - 1);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[device]) {
+        void *p = nullptr;
+        QL_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_ptr[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_static_ptr[device]);
+    return QLDPC_OK;
+}
+
+}  // namespace
+
+extern "C" int qldpc_decode_batch_host_static(qldpc_decoder *d, const uint64_t *syndromes,
+                                              int64_t B, uint64_t *corrections,
+                                              int32_t *legs_used, uint8_t *converged,
+                                              int32_t *iters) {
+    g_last_error.clear();
+    int rc = check_batch(d, syndromes, B, corrections);
+    if (rc) return rc;
+    if (d->kernel != QLDPC_KERNEL_FUSED)
+        return fail(QLDPC_ERR_UNSUPPORTED, "the static-scratch path runs the fused kernel only");
+    if (B == 0) return QLDPC_OK;
+    const int sw = (d->M + 63) / 64, cw = (d->N + 63) / 64;
+    const size_t s_cnt = 256, s_syn = align_up(8 * (size_t)sw * B, 256);
+    const size_t s_cor = align_up(8 * (size_t)cw * B, 256);
+    const size_t s_i32 = align_up(4 * (size_t)B, 256), s_u8 = align_up((size_t)B, 256);
+    const size_t need = s_cnt + s_syn + s_cor + 2 * s_i32 + s_u8;
+    if (need > (size_t)QLDPC_STATIC_SCRATCH_BYTES)
+        return fail(QLDPC_ERR_INVALID_ARG,
+                    "a batch of %lld shots needs %zu bytes of static scratch, above the %d-byte "
+                    "maximum (at most %lld shots of this code per call)",
+                    (long long)B, need, QLDPC_STATIC_SCRATCH_BYTES,
+                    (long long)(((size_t)QLDPC_STATIC_SCRATCH_BYTES - s_cnt - 6 * 256) /
+                                (8 * (size_t)(sw + cw) + 9)));
+    DeviceGuard guard(d->device);
+    QL_CUDA(guard.err);
+    unsigned char *base = nullptr;
+    rc = static_scratch(d->device, &base);
+    if (rc) return rc;
+    unsigned int *counter = reinterpret_cast<unsigned int *>(base);
+    uint64_t *dsyn = reinterpret_cast<uint64_t *>(base + s_cnt);
+    uint64_t *dcor = reinterpret_cast<uint64_t *>(base + s_cnt + s_syn);
+    int32_t *dlegs = reinterpret_cast<int32_t *>(base + s_cnt + s_syn + s_cor);
+    int32_t *diters = reinterpret_cast<int32_t *>(base + s_cnt + s_syn + s_cor + s_i32);
+    uint8_t *dconv = reinterpret_cast<uint8_t *>(base + s_cnt + s_syn + s_cor + 2 * s_i32);
+    cudaStream_t st = d->stream;
+    QL_CUDA(cudaMemcpyAsync(dsyn, syndromes, 8 * (size_t)sw * B, cudaMemcpyHostToDevice, st));
+    QL_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), st));  // the work counter starts at 0
+    const int grid = (int)std::min<int64_t>(d->grid, B);
+    QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, dsyn, (int)B,
+                                 DecodeOut{dcor, legs_used ? dlegs : nullptr,
+                                           converged ? dconv : nullptr, iters ? diters : nullptr},
+                                 counter));
+    QL_CUDA(cudaMemcpyAsync(corrections, dcor, 8 * (size_t)cw * B, cudaMemcpyDeviceToHost, st));
+    if (legs_used) QL_CUDA(cudaMemcpyAsync(legs_used, dlegs, 4 * (size_t)B, cudaMemcpyDeviceToHost, st));
+    if (iters) QL_CUDA(cudaMemcpyAsync(iters, diters, 4 * (size_t)B, cudaMemcpyDeviceToHost, st));
+    if (converged) QL_CUDA(cudaMemcpyAsync(converged, dconv, (size_t)B, cudaMemcpyDeviceToHost, st));
+    QL_CUDA(cudaStreamSynchronize(st));
+    return QLDPC_OK;
+}
+
+extern "C" {
 
 int qldpc_trace_first_leg(qldpc_decoder *d, const uint64_t *syndromes, int64_t B, int32_t T,
                           float *marginals, float *nu, float *mu, void *stream) {

@@ -26,8 +26,9 @@ QLDPC_KERNEL_BASELINE = 1
 QLDPC_KERNEL_FUSED = 2
 
 EXPORTED = ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
-            "qldpc_trace_first_leg", "qldpc_get_info", "qldpc_destroy", "qldpc_status_string",
-            "qldpc_last_error")
+            "qldpc_decode_batch_host_static", "qldpc_trace_first_leg", "qldpc_get_info",
+            "qldpc_destroy", "qldpc_status_string", "qldpc_last_error")
+QLDPC_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
 
 
 class qldpc_relay_params(ctypes.Structure):
@@ -80,6 +81,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                  ctypes.POINTER(qldpc_relay_params), ctypes.c_int]
     lib.qldpc_decode_batch.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P]
     lib.qldpc_decode_batch_host.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
+    lib.qldpc_decode_batch_host_static.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
     lib.qldpc_trace_first_leg.argtypes = [P, P, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
     lib.qldpc_get_info.argtypes = [P, ctypes.POINTER(qldpc_info)]
     lib.qldpc_destroy.argtypes = [P]
@@ -89,7 +91,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qldpc_last_error.argtypes = []
     lib.qldpc_last_error.restype = ctypes.c_char_p
     for name in ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
-                 "qldpc_trace_first_leg", "qldpc_get_info"):
+                 "qldpc_decode_batch_host_static", "qldpc_trace_first_leg", "qldpc_get_info"):
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -134,6 +136,15 @@ def qldpc_decode_batch_host(h, syndromes_ptr, B, corrections_ptr, legs_ptr=None,
     _check(load_library().qldpc_decode_batch_host(h, syndromes_ptr, int(B), corrections_ptr,
                                                   legs_ptr, conv_ptr, iters_ptr),
            "qldpc_decode_batch_host")
+
+
+def qldpc_decode_batch_host_static(h, syndromes_ptr, B, corrections_ptr, legs_ptr=None,
+                                   conv_ptr=None, iters_ptr=None):
+    """Host-buffer decode that allocates nothing (static device scratch; see qldpc.h)."""
+    _check(load_library().qldpc_decode_batch_host_static(h, syndromes_ptr, int(B),
+                                                         corrections_ptr, legs_ptr, conv_ptr,
+                                                         iters_ptr),
+           "qldpc_decode_batch_host_static")
 
 
 def qldpc_trace_first_leg(h, syndromes_ptr, B, T, marg_ptr=None, nu_ptr=None, mu_ptr=None,
