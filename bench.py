@@ -171,6 +171,31 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
+def traffic_per_launch(args):
+    """DRAM bytes (read + write) of one decode launch, from the committed ncu summary.
+
+    profiles/fused_decode_gross_T12.md records dram__bytes_read.sum and
+    dram__bytes_write.sum for a 20,000-shot launch of the same kernel; DRAM traffic
+    (syndromes in, corrections out, graph and gamma rows) grows with the shot count,
+    so it is scaled to the benchmark's shots.  None when the summary is absent or
+    was taken on a different kernel build.
+    """
+    path = os.path.join(ROOT, "profiles", "fused_decode_gross_T12.md")
+    if not os.path.exists(path):
+        return None
+    rd = wr = shots = None
+    for line in open(path):
+        if line.startswith("| dram__bytes_read.sum"):
+            rd = float(line.split("|")[2])
+        elif line.startswith("| dram__bytes_write.sum"):
+            wr = float(line.split("|")[2])
+        elif line.startswith("| shots per launch"):
+            shots = float(line.split("|")[2])
+    if rd is None or wr is None or not shots:
+        return None
+    return (rd + wr) * SHOTS / shots
+
+
 def timed_decode(dec, syn, out, steps, warmup, stream, flush):
     """Per-step CUDA-event times (ms) of the decode call, L2 flushed between steps."""
     import torch
@@ -274,18 +299,26 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    # roofline of the decode kernel: algorithmic shared-memory message traffic, four
-    # message accesses (read nu, write mu, read mu, write nu) per edge per iteration
-    msg_bytes = 4
-    alg_bytes = 4 * msg_bytes * P.E * total_iters
-    achieved = alg_bytes / (ms / 1e3) / 1e9
+    # roofline of the decode kernel.  The kernel is bound by instruction issue (the
+    # profile shows the ALU pipe and issue slots as the busiest units, DRAM idle), so
+    # the figure is algorithmic lane-operations per second against the derived ALU
+    # peak: 13 operations per edge per iteration (check node: |nu|, the two-smallest
+    # update (3), sign parity, magnitude select, sign apply = 7; fault node: marginal
+    # add, excluded-sum add, two clamp ops, memory-term share = 5; syndrome XOR = 1).
+    ops_per_edge_iter = 13
+    alg_ops = ops_per_edge_iter * P.E * total_iters
+    achieved = alg_ops / (ms / 1e3) / 1e12
     sms = dec.info.num_sms
-    peak = 128 * sms * 2070e6 / 1e9      # 128 B/clk/SM of shared memory at the 2070 MHz max clock
-    roofline = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "note": f"algorithmic bytes = 4 x {msg_bytes} B x E x iterations "
-                        f"({alg_bytes / 1e9:.2f} GB per launch); peak derived from "
-                        f"{sms} SMs x 128 B/clk x 2070 MHz"}
+    peak = 128 * sms * 2070e6 / 1e12     # 128 lanes/clk/SM (4 schedulers x 32) at 2070 MHz
+    smem_bytes = 4 * 4 * P.E * total_iters   # read nu, write mu, read mu, write nu (float32)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": traffic_per_launch(args),
+                "peak_kind": "derived: 128 lanes/clk/SM x %d SMs x 2070 MHz" % sms,
+                "algorithmic": f"{ops_per_edge_iter} ops x E={P.E} x {total_iters} iterations "
+                               f"= {alg_ops / 1e9:.1f} G ops per launch",
+                "smem_message_bytes_per_launch": smem_bytes,
+                "smem_GBps": smem_bytes / (ms / 1e3) / 1e9,
+                "smem_peak_GBps": 128 * sms * 2070e6 / 1e9}
 
     # variants measured in the same run: FP16 messages and the plain baseline kernel
     variants = {}
