@@ -178,20 +178,26 @@ def traffic_per_launch(args):
     dram__bytes_write.sum for a 20,000-shot launch of the same kernel; DRAM traffic
     (syndromes in, corrections out, graph and gamma rows) grows with the shot count,
     so it is scaled to the benchmark's shots.  None when the summary is absent or
-    was taken on a different kernel build.
+    was taken on a different kernel source (its sha1 is recorded in the summary).
     """
+    import hashlib
     path = os.path.join(ROOT, "profiles", "fused_decode_gross_T12.md")
+    src = os.path.join(ROOT, "paper_2511_21660_gb300", "csrc", "relay_fused.cu")
     if not os.path.exists(path):
         return None
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
     rd = wr = shots = None
+    same_source = False
     for line in open(path):
-        if line.startswith("| dram__bytes_read.sum"):
+        if line.startswith("| kernel source sha1"):
+            same_source = line.split("|")[2].strip() == sha
+        elif line.startswith("| dram__bytes_read.sum"):
             rd = float(line.split("|")[2])
         elif line.startswith("| dram__bytes_write.sum"):
             wr = float(line.split("|")[2])
         elif line.startswith("| shots per launch"):
             shots = float(line.split("|")[2])
-    if rd is None or wr is None or not shots:
+    if not same_source or rd is None or wr is None or not shots:
         return None
     return (rd + wr) * SHOTS / shots
 
