@@ -162,6 +162,60 @@ int qldpc_decode_batch_host_static(qldpc_decoder *d, const uint64_t *syndromes, 
 int qldpc_trace_first_leg(qldpc_decoder *d, const uint64_t *syndromes, int64_t B, int32_t T,
                           float *marginals, float *nu, float *mu, void *stream);
 
+/* ---- Soft DMem-BP: differentiable unrolled leg for tuning memory strengths ---------
+ *
+ * One leg of Relay's DMem-BP (paper Sec. 2.3, "Relay decoding": memory rule
+ * lambda_j(t) = (1-gamma_j) w_j + gamma_j Lambda_j(t-1), fault->check and marginal
+ * sums as in Relay) with the min-sum check rule replaced by sum-product and scaled per
+ * iteration (the paper trains nothing; these are this library's choices):
+ *     mu_e(t) = alpha_t (-1)^sigma_i 2 atanh(prod_{e' != e} tanh(nu_e'(t-1)/2)),
+ * with the product clamped to |.| <= 1 - eps (eps = 2^-23 in FP32, 1e-15 in FP64),
+ * run for `iterations` iterations from nu(0) = Lambda(0) = w with no early exit.
+ * Loss: mean over shots b and faults j of
+ *     F_bj softplus(Lambda_bj(T)) + (1 - F_bj) softplus(-Lambda_bj(T)),
+ * i.e. binary cross-entropy of sigmoid(-Lambda) against the true faults F.
+ * The backward pass is a hand-written adjoint that recomputes each segment of
+ * checkpoint_every iterations from the checkpoints stored by the forward pass.
+ */
+#define QLDPC_REAL_FP32 0
+#define QLDPC_REAL_FP64 1
+
+typedef struct qldpc_soft qldpc_soft; /* opaque */
+
+/* Create for H (CSR, host, copied) and priors (host, in (0,1)); fault degree <= 8,
+ * check degree <= 32.  real_type: QLDPC_REAL_FP32 or QLDPC_REAL_FP64 (the type of
+ * every real array passed to forward/backward).  Errors: INVALID_ARG, UNSUPPORTED
+ * (degrees, or state above the shared-memory limit), OOM, CUDA. */
+int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row_ptr,
+                      const int32_t *col_idx, const double *priors, int32_t iterations,
+                      int32_t checkpoint_every, int32_t real_type, int device);
+
+/* Bytes of device workspace a batch of B shots needs (checkpoints, segment buffer,
+ * per-shot partial results).  The caller allocates it. */
+int qldpc_soft_workspace_bytes(const qldpc_soft *s, int64_t B, uint64_t *bytes);
+
+/* Forward.  Device pointers: syndromes [B][ceil(M/64)] uint64, faults [B][ceil(N/64)]
+ * uint64 (the true F for the loss), gamma [N], alpha [iterations], loss [1], marginals
+ * [B][N] (Lambda(T), may be NULL), workspace (>= qldpc_soft_workspace_bytes).  Stores
+ * the checkpoints for qldpc_soft_backward in the workspace.  Asynchronous on stream.
+ * Errors: INVALID_ARG, CUDA. */
+int qldpc_soft_forward(qldpc_soft *s, const uint64_t *syndromes, const uint64_t *faults,
+                       int64_t B, const void *gamma, const void *alpha, void *loss,
+                       void *marginals, void *workspace, uint64_t workspace_bytes,
+                       void *stream);
+
+/* Backward: grad_gamma [N] = loss_grad * dloss/dgamma, grad_alpha [iterations] =
+ * loss_grad * dloss/dalpha (device; loss_grad is a device scalar, NULL means 1).
+ * Must follow qldpc_soft_forward with the same inputs and workspace.  Gradients are
+ * summed over shots in a fixed order (deterministic).  Errors: INVALID_ARG, CUDA. */
+int qldpc_soft_backward(qldpc_soft *s, const uint64_t *syndromes, const uint64_t *faults,
+                        int64_t B, const void *gamma, const void *alpha, const void *loss_grad,
+                        void *grad_gamma, void *grad_alpha, void *workspace,
+                        uint64_t workspace_bytes, void *stream);
+
+/* Free the soft handle (syncs through cudaFree).  NULL is ignored. */
+void qldpc_soft_destroy(qldpc_soft *s);
+
 /* Fill *info.  Errors: INVALID_ARG. */
 int qldpc_get_info(const qldpc_decoder *d, qldpc_info *info);
 

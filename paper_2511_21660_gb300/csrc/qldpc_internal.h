@@ -101,4 +101,33 @@ const void *baseline_fn();
 cudaError_t launch_baseline(int B, int threads, size_t smem, cudaStream_t st, const BaseGraph &g,
                             const DevParams &p, const uint64_t *syn, DecodeOut out);
 
+// ---- soft DMem-BP (sum-product, trainable memory strengths) ------------------------
+
+// CSR / CSC graph of the soft kernels (device pointers).
+struct SoftGraph {
+    int M, N, E;
+    int syn_words, cor_words;
+    const int32_t *row_ptr;    // [M+1]
+    const int32_t *col_idx;    // [E]
+    const int32_t *var_ptr;    // [N+1]
+    const int32_t *var_edges;  // [E] edges of fault j in increasing edge order
+};
+
+// Everything one soft forward or backward launch needs (device pointers; real
+// arrays are float or double according to fp64).
+struct SoftLaunch {
+    SoftGraph g;
+    int fp64, dc_max, T_it, K, B;
+    double eps;
+    const uint64_t *syn, *faults;
+    const void *gamma, *alpha, *w, *upstream;
+    void *ckpt, *seg, *shot_loss, *shot_gg, *shot_ga;
+    void *loss, *marg, *grad_gamma, *grad_alpha;
+};
+
+size_t soft_smem_forward(const SoftGraph &g, int fp64);
+size_t soft_smem_backward(const SoftGraph &g, int T_it, int fp64);
+cudaError_t soft_run_forward(const SoftLaunch &L, cudaStream_t st);
+cudaError_t soft_run_backward(const SoftLaunch &L, cudaStream_t st);
+
 }  // namespace qldpc

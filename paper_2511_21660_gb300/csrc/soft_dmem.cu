@@ -1,0 +1,391 @@
+// Soft DMem-BP: one unrolled leg of disordered-memory belief propagation with the
+// sum-product check rule, its BCE loss and a hand-written adjoint (reverse mode)
+// with checkpointing.  The memory rule and message structure are Relay's (paper
+// Sec. 2.3, "Relay decoding"); the sum-product rule, the per-iteration scale
+// alpha_t, the trainable gamma_j and the loss are this library's readings:
+//   nu_e(0) = Lambda_j(0) = w_j
+//   lambda_j(t) = (1 - gamma_j) w_j + gamma_j Lambda_j(t-1)
+//   P_e = prod_{e' in row, e' != e} tanh(nu_e'(t-1)/2) clamped to |P_e| <= 1 - eps
+//   mu_e(t) = alpha_t (-1)^sigma_i 2 atanh(P_e)
+//   nu_e(t) = lambda_j(t) + sum_{e' in col(j), e' != e} mu_e'(t);  Lambda_j(t) = lambda_j(t) + sum mu
+//   loss = mean_{b, j} [F_j softplus(Lambda_j(T)) + (1 - F_j) softplus(-Lambda_j(T))]
+//
+// One block per shot.  The forward keeps nu (edge order of the CSR) and Lambda in
+// shared memory and stores them every K iterations (checkpoints).  The adjoint
+// walks the checkpoint segments backwards: it recomputes the segment's forward from
+// its checkpoint, keeping each iteration's nu(t-1), Lambda(t-1) in a global
+// segment buffer, then runs the reverse iterations.  Per-shot gradients are summed
+// over shots in a fixed order, so results are deterministic.
+#include "qldpc_internal.h"
+
+namespace qldpc {
+namespace {
+
+constexpr int SOFT_THREADS = 256;
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+struct RM;
+template <>
+struct RM<float> {
+    static __device__ __forceinline__ float tanh_(float x) { return tanhf(x); }
+    static __device__ __forceinline__ float atanh_(float x) { return atanhf(x); }
+    static __device__ __forceinline__ float softplus(float x) {
+        return x > 0.0f ? x + log1pf(expf(-x)) : log1pf(expf(x));
+    }
+    static __device__ __forceinline__ float sigmoid(float x) {
+        return x >= 0.0f ? 1.0f / (1.0f + expf(-x)) : expf(x) / (1.0f + expf(x));
+    }
+};
+template <>
+struct RM<double> {
+    static __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
+    static __device__ __forceinline__ double atanh_(double x) { return atanh(x); }
+    static __device__ __forceinline__ double softplus(double x) {
+        return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x));
+    }
+    static __device__ __forceinline__ double sigmoid(double x) {
+        return x >= 0.0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x));
+    }
+};
+
+template <typename T>
+struct SoftArgs {
+    SoftGraph g;
+    int T_it, K, nck;
+    T eps;
+    const uint64_t *syn, *faults;
+    int B;
+    const T *gamma, *alpha, *w;
+    T *ckpt;       // [B][nck][E+N]
+    T *seg;        // [B][K][E+N]
+    T *shot_loss;  // [B]
+    T *shot_gg;    // [B][N]
+    T *shot_ga;    // [B][T]
+    T *marg;       // [B][N] or nullptr
+};
+
+__device__ __forceinline__ uint32_t bit_of(const uint64_t *v, int i) {
+    return (uint32_t)((v[i >> 6] >> (i & 63)) & 1ull);
+}
+
+// Sum of one value per thread in a fixed order (warp shuffles, then warp 0):
+// deterministic.  Every thread must call it; thread 0 gets the total.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T s = 0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < SOFT_THREADS / 32; ++q) s += red[q];
+    __syncthreads();
+    return s;
+}
+
+// Check products of one row: P_k = prod_{l != k} tanh(nu_l/2), clamped.  The row
+// has d <= DCM edges.
+template <typename T, int DCM>
+__device__ __forceinline__ void row_products(const T *nu_row, int d, T eps, T (&tau)[DCM],
+                                             T (&P)[DCM], bool (&cl)[DCM]) {
+#pragma unroll
+    for (int k = 0; k < DCM; ++k) tau[k] = k < d ? RM<T>::tanh_(nu_row[k] / T(2)) : T(1);
+#pragma unroll
+    for (int k = 0; k < DCM; ++k) {
+        T prod = T(1);
+#pragma unroll
+        for (int l = 0; l < DCM; ++l)
+            if (l != k && l < d) prod *= tau[l];
+        cl[k] = false;
+        if (prod > T(1) - eps) {
+            prod = T(1) - eps;
+            cl[k] = true;
+        }
+        if (prod < -(T(1) - eps)) {
+            prod = -(T(1) - eps);
+            cl[k] = true;
+        }
+        P[k] = prod;
+    }
+}
+
+// One forward iteration t (1-based) on the shared state nu[E], Lam[N] (in place).
+template <typename T, int DCM>
+__device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint64_t *sy, int t,
+                                               T *nu, T *Lam) {
+    const SoftGraph &g = a.g;
+    const T at = a.alpha[t - 1];
+    for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
+        const int e0 = g.row_ptr[i], d = g.row_ptr[i + 1] - e0;
+        T tau[DCM], P[DCM];
+        bool cl[DCM];
+        row_products<T, DCM>(nu + e0, d, a.eps, tau, P, cl);
+        const T s = bit_of(sy, i) ? T(-2) : T(2);
+#pragma unroll
+        for (int k = 0; k < DCM; ++k)
+            if (k < d) nu[e0 + k] = at * s * RM<T>::atanh_(P[k]);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
+        const int b = g.var_ptr[j], d = g.var_ptr[j + 1] - b;
+        const T lam = (T(1) - a.gamma[j]) * a.w[j] + a.gamma[j] * Lam[j];
+        T mu[8];
+        for (int k = 0; k < d; ++k) mu[k] = nu[g.var_edges[b + k]];
+        T L = lam;
+        for (int k = 0; k < d; ++k) L += mu[k];
+        Lam[j] = L;
+        for (int k = 0; k < d; ++k) {
+            T v = lam;
+            for (int k2 = 0; k2 < d; ++k2)
+                if (k2 != k) v += mu[k2];
+            nu[g.var_edges[b + k]] = v;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void init_state(const SoftArgs<T> &a, T *nu, T *Lam) {
+    const SoftGraph &g = a.g;
+    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) Lam[j] = a.w[j];
+    for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nu[e] = a.w[g.col_idx[e]];
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_state(const T *src_nu, const T *src_L, T *dst, int E, int N) {
+    for (int e = threadIdx.x; e < E; e += SOFT_THREADS) dst[e] = src_nu[e];
+    for (int j = threadIdx.x; j < N; j += SOFT_THREADS) dst[E + j] = src_L[j];
+}
+
+template <typename T, int DCM>
+__global__ void __launch_bounds__(SOFT_THREADS) soft_forward(SoftArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SoftGraph &g = a.g;
+    T *nu = reinterpret_cast<T *>(smem_raw);
+    T *Lam = nu + g.E;
+    __shared__ T red[SOFT_THREADS / 32];
+    const int b = blockIdx.x;
+    const uint64_t *sy = a.syn + (size_t)b * g.syn_words;
+    const uint64_t *fy = a.faults + (size_t)b * g.cor_words;
+    const size_t EN = (size_t)g.E + g.N;
+    init_state(a, nu, Lam);
+    for (int t = 1; t <= a.T_it; ++t) {
+        if ((t - 1) % a.K == 0)
+            copy_state(nu, Lam, a.ckpt + ((size_t)b * a.nck + (t - 1) / a.K) * EN, g.E, g.N);
+        soft_iteration<T, DCM>(a, sy, t, nu, Lam);
+    }
+    T part = 0;
+    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
+        part += bit_of(fy, j) ? RM<T>::softplus(Lam[j]) : RM<T>::softplus(-Lam[j]);
+        if (a.marg) a.marg[(size_t)b * g.N + j] = Lam[j];
+    }
+    const T tot = block_sum(part, red);
+    if (threadIdx.x == 0) a.shot_loss[b] = tot;
+}
+
+// Adjoint.  Shared memory: nu[E], Lam[N] (forward recompute), nb[E] (adjoint of
+// nu(t), then of mu(t)), Lb[N] (adjoint of Lambda), gs[N] (gamma gradient of the
+// shot), as[T] (alpha gradient of the shot).
+template <typename T, int DCM>
+__global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SoftGraph &g = a.g;
+    T *nu = reinterpret_cast<T *>(smem_raw);
+    T *Lam = nu + g.E;
+    T *nb = Lam + g.N;
+    T *Lb = nb + g.E;
+    T *gs = Lb + g.N;
+    T *as = gs + g.N;
+    __shared__ T red[SOFT_THREADS / 32];
+    const int b = blockIdx.x;
+    const uint64_t *sy = a.syn + (size_t)b * g.syn_words;
+    const uint64_t *fy = a.faults + (size_t)b * g.cor_words;
+    const size_t EN = (size_t)g.E + g.N;
+    T *segb = a.seg + (size_t)b * a.K * EN;
+    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) gs[j] = 0;
+    for (int t = threadIdx.x; t < a.T_it; t += SOFT_THREADS) as[t] = 0;
+
+    for (int s = a.nck - 1; s >= 0; --s) {
+        const int t0 = s * a.K, t1 = min(a.T_it, t0 + a.K);
+        const T *ck = a.ckpt + ((size_t)b * a.nck + s) * EN;
+        for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nu[e] = ck[e];
+        for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) Lam[j] = ck[g.E + j];
+        __syncthreads();
+        for (int t = t0 + 1; t <= t1; ++t) {
+            copy_state(nu, Lam, segb + (size_t)(t - t0 - 1) * EN, g.E, g.N);
+            soft_iteration<T, DCM>(a, sy, t, nu, Lam);
+        }
+        if (s == a.nck - 1) {  // Lambda(T) is in Lam: adjoint of the loss sum
+            for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS)
+                Lb[j] = RM<T>::sigmoid(Lam[j]) - (bit_of(fy, j) ? T(0) : T(1));
+            for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nb[e] = 0;
+        }
+        __syncthreads();
+        for (int t = t1; t > t0; --t) {
+            const T *nu_prev = segb + (size_t)(t - t0 - 1) * EN;
+            const T *L_prev = nu_prev + g.E;
+            const bool inner = t - 1 >= 1;
+            // fault adjoint: lambda_bar = Lb + sum nb;  mu_bar_e = lambda_bar - nb_e
+            for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
+                const int e0 = g.var_ptr[j], d = g.var_ptr[j + 1] - e0;
+                T sum = 0;
+                for (int k = 0; k < d; ++k) sum += nb[g.var_edges[e0 + k]];
+                const T lb = Lb[j] + sum;
+                for (int k = 0; k < d; ++k) {
+                    const int e = g.var_edges[e0 + k];
+                    nb[e] = lb - nb[e];
+                }
+                gs[j] += lb * (L_prev[j] - a.w[j]);
+                Lb[j] = inner ? lb * a.gamma[j] : T(0);
+            }
+            __syncthreads();
+            // check adjoint: mu_e = alpha_t s 2 atanh(P_e)
+            const T at = a.alpha[t - 1];
+            T apart = 0;
+            for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
+                const int e0 = g.row_ptr[i], d = g.row_ptr[i + 1] - e0;
+                T tau[DCM], P[DCM], Pb[DCM];
+                bool cl[DCM];
+                row_products<T, DCM>(nu_prev + e0, d, a.eps, tau, P, cl);
+                const T s2 = bit_of(sy, i) ? T(-2) : T(2);
+#pragma unroll
+                for (int k = 0; k < DCM; ++k) {
+                    Pb[k] = 0;
+                    if (k < d) {
+                        const T mb = nb[e0 + k];
+                        apart += mb * s2 * RM<T>::atanh_(P[k]);
+                        if (!cl[k]) Pb[k] = mb * at * s2 / (T(1) - P[k] * P[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < DCM; ++k) {
+                    if (k < d) {
+                        T tb = 0;
+#pragma unroll
+                        for (int m = 0; m < DCM; ++m) {
+                            if (m == k || m >= d) continue;
+                            T rest = Pb[m];
+#pragma unroll
+                            for (int l = 0; l < DCM; ++l)
+                                if (l != m && l != k && l < d) rest *= tau[l];
+                            tb += rest;
+                        }
+                        nb[e0 + k] = inner ? tb * (T(1) - tau[k] * tau[k]) / T(2) : T(0);
+                    }
+                }
+            }
+            const T asum = block_sum(apart, red);  // includes the barrier
+            if (threadIdx.x == 0) as[t - 1] += asum;
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) a.shot_gg[(size_t)b * g.N + j] = gs[j];
+    for (int t = threadIdx.x; t < a.T_it; t += SOFT_THREADS) a.shot_ga[(size_t)b * a.T_it + t] = as[t];
+}
+
+// out[c] = scale * upstream * sum_b in[b][c], summed over b in order.
+template <typename T>
+__global__ void reduce_shots(const T *in, int B, int n, T scale, const T *upstream, T *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    T s = 0;
+    for (int b = 0; b < B; ++b) s += in[(size_t)b * n + c];
+    out[c] = s * scale * (upstream ? *upstream : T(1));
+}
+
+template <typename T>
+size_t fwd_smem(const SoftGraph &g) { return sizeof(T) * ((size_t)g.E + g.N); }
+template <typename T>
+size_t bwd_smem(const SoftGraph &g, int Tit) {
+    return sizeof(T) * (2 * ((size_t)g.E + g.N) + g.N + Tit);
+}
+
+template <typename T, int DCM>
+cudaError_t run_forward_t(const SoftLaunch &L, cudaStream_t st) {
+    SoftArgs<T> a{};
+    a.g = L.g;
+    a.T_it = L.T_it;
+    a.K = L.K;
+    a.nck = (L.T_it + L.K - 1) / L.K;
+    a.eps = (T)L.eps;
+    a.syn = L.syn;
+    a.faults = L.faults;
+    a.B = L.B;
+    a.gamma = static_cast<const T *>(L.gamma);
+    a.alpha = static_cast<const T *>(L.alpha);
+    a.w = static_cast<const T *>(L.w);
+    a.ckpt = static_cast<T *>(L.ckpt);
+    a.seg = static_cast<T *>(L.seg);
+    a.shot_loss = static_cast<T *>(L.shot_loss);
+    a.shot_gg = static_cast<T *>(L.shot_gg);
+    a.shot_ga = static_cast<T *>(L.shot_ga);
+    a.marg = static_cast<T *>(L.marg);
+    const size_t sm = fwd_smem<T>(L.g);
+    cudaError_t e = cudaFuncSetAttribute(soft_forward<T, DCM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    soft_forward<T, DCM><<<L.B, SOFT_THREADS, sm, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const T scale = T(1) / ((T)L.B * (T)L.g.N);
+    reduce_shots<T><<<1, 32, 0, st>>>(a.shot_loss, L.B, 1, scale, nullptr,
+                                      static_cast<T *>(L.loss));
+    return cudaGetLastError();
+}
+
+template <typename T, int DCM>
+cudaError_t run_backward_t(const SoftLaunch &L, cudaStream_t st) {
+    SoftArgs<T> a{};
+    a.g = L.g;
+    a.T_it = L.T_it;
+    a.K = L.K;
+    a.nck = (L.T_it + L.K - 1) / L.K;
+    a.eps = (T)L.eps;
+    a.syn = L.syn;
+    a.faults = L.faults;
+    a.B = L.B;
+    a.gamma = static_cast<const T *>(L.gamma);
+    a.alpha = static_cast<const T *>(L.alpha);
+    a.w = static_cast<const T *>(L.w);
+    a.ckpt = static_cast<T *>(L.ckpt);
+    a.seg = static_cast<T *>(L.seg);
+    a.shot_loss = static_cast<T *>(L.shot_loss);
+    a.shot_gg = static_cast<T *>(L.shot_gg);
+    a.shot_ga = static_cast<T *>(L.shot_ga);
+    const size_t sm = bwd_smem<T>(L.g, L.T_it);
+    cudaError_t e = cudaFuncSetAttribute(soft_backward<T, DCM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    soft_backward<T, DCM><<<L.B, SOFT_THREADS, sm, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const T scale = T(1) / ((T)L.B * (T)L.g.N);
+    const T *up = static_cast<const T *>(L.upstream);
+    reduce_shots<T><<<(L.g.N + 127) / 128, 128, 0, st>>>(a.shot_gg, L.B, L.g.N, scale, up,
+                                                         static_cast<T *>(L.grad_gamma));
+    reduce_shots<T><<<(L.T_it + 127) / 128, 128, 0, st>>>(a.shot_ga, L.B, L.T_it, scale, up,
+                                                          static_cast<T *>(L.grad_alpha));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t soft_smem_forward(const SoftGraph &g, int fp64) {
+    return fp64 ? fwd_smem<double>(g) : fwd_smem<float>(g);
+}
+size_t soft_smem_backward(const SoftGraph &g, int T_it, int fp64) {
+    return fp64 ? bwd_smem<double>(g, T_it) : bwd_smem<float>(g, T_it);
+}
+
+cudaError_t soft_run_forward(const SoftLaunch &L, cudaStream_t st) {
+    if (L.fp64) return L.dc_max <= 8 ? run_forward_t<double, 8>(L, st) : run_forward_t<double, 32>(L, st);
+    return L.dc_max <= 8 ? run_forward_t<float, 8>(L, st) : run_forward_t<float, 32>(L, st);
+}
+
+cudaError_t soft_run_backward(const SoftLaunch &L, cudaStream_t st) {
+    if (L.fp64) return L.dc_max <= 8 ? run_backward_t<double, 8>(L, st) : run_backward_t<double, 32>(L, st);
+    return L.dc_max <= 8 ? run_backward_t<float, 8>(L, st) : run_backward_t<float, 32>(L, st);
+}
+
+}  // namespace qldpc

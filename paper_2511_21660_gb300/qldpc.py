@@ -27,7 +27,11 @@ QLDPC_KERNEL_FUSED = 2
 
 EXPORTED = ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
             "qldpc_decode_batch_host_static", "qldpc_trace_first_leg", "qldpc_get_info",
-            "qldpc_destroy", "qldpc_status_string", "qldpc_last_error")
+            "qldpc_destroy", "qldpc_status_string", "qldpc_last_error", "qldpc_soft_create",
+            "qldpc_soft_workspace_bytes", "qldpc_soft_forward", "qldpc_soft_backward",
+            "qldpc_soft_destroy")
+QLDPC_REAL_FP32 = 0
+QLDPC_REAL_FP64 = 1
 QLDPC_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
 
 
@@ -90,8 +94,18 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qldpc_status_string.restype = ctypes.c_char_p
     lib.qldpc_last_error.argtypes = []
     lib.qldpc_last_error.restype = ctypes.c_char_p
+    lib.qldpc_soft_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, P, P, P,
+                                      ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]
+    lib.qldpc_soft_workspace_bytes.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
+    lib.qldpc_soft_forward.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P, P, ctypes.c_uint64, P]
+    lib.qldpc_soft_backward.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P, P, P,
+                                        ctypes.c_uint64, P]
+    lib.qldpc_soft_destroy.argtypes = [P]
+    lib.qldpc_soft_destroy.restype = None
     for name in ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
-                 "qldpc_decode_batch_host_static", "qldpc_trace_first_leg", "qldpc_get_info"):
+                 "qldpc_decode_batch_host_static", "qldpc_trace_first_leg", "qldpc_get_info",
+                 "qldpc_soft_create", "qldpc_soft_workspace_bytes", "qldpc_soft_forward",
+                 "qldpc_soft_backward"):
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -280,3 +294,153 @@ class RelayDecoder:
                               ctypes.c_void_p(mu.data_ptr()) if messages else None,
                               self._stream_ptr(stream))
         return marg, nu, mu
+
+
+# ---- soft DMem-BP (differentiable leg) ----------------------------------------------
+
+def qldpc_soft_create(M, N, row_ptr, col_idx, priors, iterations, checkpoint_every, real_type,
+                      device=0):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    pr = np.ascontiguousarray(priors, dtype=np.float64)
+    _check(lib.qldpc_soft_create(ctypes.byref(h), int(M), int(N), rp.ctypes.data, ci.ctypes.data,
+                                 pr.ctypes.data, int(iterations), int(checkpoint_every),
+                                 int(real_type), int(device)), "qldpc_soft_create")
+    return h
+
+
+def qldpc_soft_workspace_bytes(h, B) -> int:
+    n = ctypes.c_uint64()
+    _check(load_library().qldpc_soft_workspace_bytes(h, int(B), ctypes.byref(n)),
+           "qldpc_soft_workspace_bytes")
+    return int(n.value)
+
+
+def qldpc_soft_forward(h, syn_ptr, faults_ptr, B, gamma_ptr, alpha_ptr, loss_ptr, marg_ptr,
+                       ws_ptr, ws_bytes, stream=None):
+    _check(load_library().qldpc_soft_forward(h, syn_ptr, faults_ptr, int(B), gamma_ptr, alpha_ptr,
+                                             loss_ptr, marg_ptr, ws_ptr, int(ws_bytes), stream),
+           "qldpc_soft_forward")
+
+
+def qldpc_soft_backward(h, syn_ptr, faults_ptr, B, gamma_ptr, alpha_ptr, loss_grad_ptr,
+                        grad_gamma_ptr, grad_alpha_ptr, ws_ptr, ws_bytes, stream=None):
+    _check(load_library().qldpc_soft_backward(h, syn_ptr, faults_ptr, int(B), gamma_ptr,
+                                              alpha_ptr, loss_grad_ptr, grad_gamma_ptr,
+                                              grad_alpha_ptr, ws_ptr, int(ws_bytes), stream),
+           "qldpc_soft_backward")
+
+
+def qldpc_soft_destroy(h) -> None:
+    if h is not None and h.value:
+        load_library().qldpc_soft_destroy(h)
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class SoftDMem:
+    """Unrolled soft DMem-BP leg on one GPU (see include/qldpc.h for the equations).
+
+    dtype: torch.float32 or torch.float64 (every real tensor passed in must match).
+    """
+
+    def __init__(self, row_ptr, col_idx, priors, iterations: int = 25,
+                 checkpoint_every: int = 5, dtype=None, device: int = 0):
+        import torch
+        self.dtype = dtype or torch.float32
+        real = QLDPC_REAL_FP64 if self.dtype == torch.float64 else QLDPC_REAL_FP32
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        self.M, self.N = row_ptr.size - 1, int(np.asarray(priors).size)
+        self.T, self.K, self.device = iterations, checkpoint_every, device
+        self.handle = qldpc_soft_create(self.M, self.N, row_ptr, col_idx, priors, iterations,
+                                        checkpoint_every, real, device)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            qldpc_soft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, B: int):
+        import torch
+        n = qldpc_soft_workspace_bytes(self.handle, B)
+        return torch.empty(n, dtype=torch.uint8, device=torch.device("cuda", self.device))
+
+    def forward(self, syndromes, faults, gamma, alpha, workspace=None, marginals=False,
+                stream=None):
+        """Returns (loss [1], Lambda(T) [B, N] or None, workspace)."""
+        import torch
+        B = syndromes.shape[0]
+        ws = workspace if workspace is not None else self.workspace(B)
+        loss = torch.empty(1, dtype=self.dtype, device=gamma.device)
+        marg = torch.empty((B, self.N), dtype=self.dtype, device=gamma.device) if marginals else None
+        st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+        qldpc_soft_forward(self.handle, _vp(syndromes), _vp(faults), B, _vp(gamma), _vp(alpha),
+                           _vp(loss), _vp(marg), _vp(ws), ws.numel(), st)
+        return loss, marg, ws
+
+    def backward(self, syndromes, faults, gamma, alpha, workspace, loss_grad=None, stream=None):
+        """Returns (grad_gamma [N], grad_alpha [T]); needs the forward's workspace."""
+        import torch
+        B = syndromes.shape[0]
+        gg = torch.empty(self.N, dtype=self.dtype, device=gamma.device)
+        ga = torch.empty(self.T, dtype=self.dtype, device=gamma.device)
+        st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+        qldpc_soft_backward(self.handle, _vp(syndromes), _vp(faults), B, _vp(gamma), _vp(alpha),
+                            _vp(loss_grad), _vp(gg), _vp(ga), _vp(workspace), workspace.numel(),
+                            st)
+        return gg, ga
+
+
+def soft_dmem_loss(soft: SoftDMem, syndromes, faults, gamma, alpha):
+    """Loss of the unrolled soft DMem-BP leg, differentiable in gamma and alpha.
+
+    syndromes / faults: int64 CUDA tensors of bit-packed words [B, ceil(M/64)] and
+    [B, ceil(N/64)]; gamma [N], alpha [T]: CUDA tensors of soft.dtype.
+    """
+    return _SoftDMemLoss.apply(gamma, alpha, soft, syndromes, faults)
+
+
+def _autograd_function():
+    import torch
+
+    class SoftDMemLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, gamma, alpha, soft, syndromes, faults):
+            gamma = gamma.contiguous()
+            alpha = alpha.contiguous()
+            loss, _, ws = soft.forward(syndromes, faults, gamma, alpha)
+            ctx.soft = soft
+            ctx.save_for_backward(gamma, alpha, syndromes, faults, ws)
+            return loss.reshape(())
+
+        @staticmethod
+        def backward(ctx, grad_loss):
+            gamma, alpha, syndromes, faults, ws = ctx.saved_tensors
+            up = grad_loss.reshape(1).to(gamma.dtype).contiguous()
+            gg, ga = ctx.soft.backward(syndromes, faults, gamma, alpha, ws, loss_grad=up)
+            return gg, ga, None, None, None
+
+    return SoftDMemLoss
+
+
+class _Lazy:
+    def __init__(self):
+        self.fn = None
+
+    def apply(self, *args):
+        if self.fn is None:
+            self.fn = _autograd_function()
+        return self.fn.apply(*args)
+
+
+_SoftDMemLoss = _Lazy()
