@@ -26,7 +26,7 @@ def _case(seed=5, B=12, T=25):
     s = syndromes_of(P.row_ptr, P.col_idx, F)
     rng = np.random.default_rng(seed)
     gam = rng.uniform(0.0, 0.3, P.N)
-    alpha = rng.uniform(0.4, 0.6, T)
+    alpha = rng.uniform(0.25, 0.4, T)   # unsaturated: no product reaches the clamp
     return P, F, s, gam, alpha
 
 
