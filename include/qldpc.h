@@ -125,6 +125,27 @@ int qldpc_decode_batch_host(qldpc_decoder *d, const uint64_t *syndromes, int64_t
                             int32_t *iters);
 
 /*
+ * Decode a mixed batch of shots of several codes in one persistent launch.
+ * decoders[0..n_codes-1] (1 <= n_codes <= 8): fused-kernel decoders created on one
+ * device with the same message precision and degree family (max check degree <= 8
+ * and max fault degree <= 4 for all, or the same wider family).  Each keeps its own
+ * graph, priors, gamma table and Relay parameters.  Device arrays:
+ * code_of_shot [B] int32 (index into decoders), syndromes [B][syndrome_stride] and
+ * corrections [B][correction_stride] uint64 rows (strides >= the widest code's
+ * ceil(M/64) and ceil(N/64); each shot uses the first words of its row), legs_used,
+ * converged, iters [B] as in qldpc_decode_batch (may be NULL).  A shot whose code id
+ * is out of range is skipped and gets iters = -1, legs = 0, converged = 0.  Uses the
+ * work counter of decoders[0]: do not overlap with other calls on that handle.
+ * Asynchronous on stream.  Errors: INVALID_ARG, UNSUPPORTED (mixed families or
+ * precisions, baseline decoders), CUDA.
+ */
+int qldpc_decode_batch_multi(qldpc_decoder *const *decoders, int32_t n_codes,
+                             const int32_t *code_of_shot, const uint64_t *syndromes,
+                             int32_t syndrome_stride, int64_t B, uint64_t *corrections,
+                             int32_t correction_stride, int32_t *legs_used, uint8_t *converged,
+                             int32_t *iters, void *stream);
+
+/*
  * Size of the static scratch area used by qldpc_decode_batch_host_static: 8 MiB of
  * device memory that every GPU loading this library holds until the process exits.
  */

@@ -6,8 +6,9 @@ raises if the library has not been built: there is no CPU fallback.
 """
 from .qldpc import (QLDPC_KERNEL_AUTO, QLDPC_KERNEL_BASELINE, QLDPC_KERNEL_FUSED,
                     QLDPC_MSG_FP16, QLDPC_MSG_FP32, QldpcError, RelayConfig, RelayDecoder,
-                    SoftDMem, load_library, soft_dmem_loss)
+                    SoftDMem, decode_mixed, load_library, soft_dmem_loss)
 
-__all__ = ["RelayDecoder", "RelayConfig", "SoftDMem", "soft_dmem_loss", "QldpcError",
+__all__ = ["RelayDecoder", "RelayConfig", "SoftDMem", "soft_dmem_loss", "decode_mixed",
+           "QldpcError",
            "load_library", "QLDPC_MSG_FP32",
            "QLDPC_MSG_FP16", "QLDPC_KERNEL_AUTO", "QLDPC_KERNEL_BASELINE", "QLDPC_KERNEL_FUSED"]

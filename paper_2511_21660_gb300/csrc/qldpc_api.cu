@@ -539,6 +539,68 @@ extern "C" int qldpc_decode_batch_host_static(qldpc_decoder *d, const uint64_t *
 
 extern "C" {
 
+int qldpc_decode_batch_multi(qldpc_decoder *const *decoders, int32_t n_codes,
+                              const int32_t *code_of_shot, const uint64_t *syndromes,
+                              int32_t syndrome_stride, int64_t B, uint64_t *corrections,
+                              int32_t correction_stride, int32_t *legs_used, uint8_t *converged,
+                              int32_t *iters, void *stream) {
+    g_last_error.clear();
+    if (!decoders || n_codes < 1 || n_codes > kMaxMultiCodes)
+        return fail(QLDPC_ERR_INVALID_ARG, "need 1..%d decoders", kMaxMultiCodes);
+    if (B < 0 || B > 0x7fffffffLL) return fail(QLDPC_ERR_INVALID_ARG, "batch size out of range");
+    if (B == 0) return QLDPC_OK;
+    if (!code_of_shot || !syndromes || !corrections)
+        return fail(QLDPC_ERR_INVALID_ARG, "code_of_shot, syndromes and corrections are required");
+    const qldpc_decoder *d0 = decoders[0];
+    int max_sw = 0, max_cw = 0, big = 0;
+    for (int c = 0; c < n_codes; ++c) {
+        const qldpc_decoder *d = decoders[c];
+        if (!d) return fail(QLDPC_ERR_INVALID_ARG, "decoder %d is NULL", c);
+        if (d->kernel != QLDPC_KERNEL_FUSED)
+            return fail(QLDPC_ERR_UNSUPPORTED, "mixed batches need fused-kernel decoders");
+        if (d->device != d0->device || d->msg_fp16 != d0->msg_fp16 || d->fk->dc != d0->fk->dc ||
+            d->fk->dv != d0->fk->dv)
+            return fail(QLDPC_ERR_UNSUPPORTED,
+                        "decoders of a mixed batch must share device, message precision and "
+                        "degree family (decoder %d differs)", c);
+        max_sw = std::max(max_sw, d->fg.syn_words);
+        max_cw = std::max(max_cw, d->fg.cor_words);
+        if (d->fg.N > decoders[big]->fg.N) big = c;
+    }
+    if (syndrome_stride < max_sw || correction_stride < max_cw)
+        return fail(QLDPC_ERR_INVALID_ARG, "row strides %d/%d below the widest code's %d/%d words",
+                    syndrome_stride, correction_stride, max_sw, max_cw);
+    DeviceGuard guard(d0->device);
+    QL_CUDA(guard.err);
+    const void *ptrs[6] = {code_of_shot, syndromes, corrections, legs_used, converged, iters};
+    for (int q = 0; q < 6; ++q)
+        if (ptrs[q] && !is_device_ptr(ptrs[q]))
+            return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
+    // the kernel instance of the code with the most faults serves every code
+    const qldpc_decoder *db = decoders[big];
+    const FusedKernel *fk = db->fk;
+    MultiTable tab{};
+    tab.n = n_codes;
+    size_t smem = 0;
+    for (int c = 0; c < n_codes; ++c) {
+        tab.g[c] = decoders[c]->fg;
+        tab.p[c] = decoders[c]->prm;
+        smem = std::max(smem, decoders[c]->smem);
+    }
+    QL_CUDA(cudaFuncSetAttribute(fk->multi_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    int bps = 0;
+    QL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fk->multi_fn, fk->threads, smem));
+    if (bps < 1) return fail(QLDPC_ERR_UNSUPPORTED, "mixed-batch kernel cannot be resident");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    QL_CUDA(cudaMemsetAsync(d0->counter, 0, sizeof(unsigned int), st));
+    const int grid = (int)std::min<int64_t>((int64_t)db->num_sms * bps, B);
+    QL_CUDA(fk->launch_multi(dim3(grid), smem, st, tab, code_of_shot, syndromes, syndrome_stride,
+                             correction_stride, (int)B,
+                             DecodeOut{corrections, legs_used, converged, iters}, d0->counter));
+    return QLDPC_OK;
+}
+
 int qldpc_trace_first_leg(qldpc_decoder *d, const uint64_t *syndromes, int64_t B, int32_t T,
                           float *marginals, float *nu, float *mu, void *stream) {
     g_last_error.clear();

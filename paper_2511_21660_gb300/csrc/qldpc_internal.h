@@ -53,6 +53,14 @@ struct BaseGraph {
     const float *gamma;        // [(R+1)][N]
 };
 
+// Per-code graphs and parameters of a mixed batch, passed by value to the kernel.
+constexpr int kMaxMultiCodes = 8;
+struct MultiTable {
+    int n;
+    FusedGraph g[kMaxMultiCodes];
+    DevParams p[kMaxMultiCodes];
+};
+
 struct DecodeOut {
     uint64_t *corr;
     int32_t *legs;
@@ -71,6 +79,11 @@ struct FusedKernel {
     cudaError_t (*launch_decode)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                                  const DevParams &p, const uint64_t *syn, int B, DecodeOut out,
                                  unsigned int *counter);
+    const void *multi_fn;    // __global__ symbol of the mixed-batch kernel
+    cudaError_t (*launch_multi)(dim3 grid, size_t smem, cudaStream_t st, const MultiTable &tab,
+                                const int32_t *code_of_shot, const uint64_t *syn,
+                                int syn_stride, int cor_stride, int B, DecodeOut out,
+                                unsigned int *counter);
     const void *trace_fn;    // __global__ symbol of the trace kernel (nullptr if none)
     cudaError_t (*launch_trace)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                                 const DevParams &p, const uint64_t *syn, int B, int T,

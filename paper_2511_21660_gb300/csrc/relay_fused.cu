@@ -413,9 +413,68 @@ __device__ __forceinline__ void load_syndrome(const FusedGraph &g, const uint64_
     }
 }
 
-// One block per shot at a time; shots come from a global counter.  Per iteration:
-// check pass | barrier | fault pass | barrier | per-warp convergence test.  A leg
-// end adds the weight reduction, the next leg's initialisation and one barrier.
+// Relay on one shot: the leg schedule around the check and fault passes.  Per
+// iteration: check pass | barrier | fault pass | barrier | per-warp convergence
+// test.  A leg end adds the weight reduction, the next leg's initialisation and one
+// barrier.  Called by every thread of the block with block-uniform arguments.
+template <typename MT, int NT, int VPT, int DC, int DV>
+__device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams &p, int shot,
+                                            const uint64_t *sy, uint64_t *cor, DecodeOut out,
+                                            unsigned char *msg, uint32_t *fw, uint32_t *sg,
+                                            uint32_t *par, float *ws, long long *s_Wpart,
+                                            float (&Lam)[VPT], float (&bb)[VPT],
+                                            float (&gg)[VPT]) {
+    const int tid = threadIdx.x;
+    const float C = p.clip;
+    load_syndrome<NT>(g, sy, sg);
+    int leg = 0, sols = 0, t = 0, pb = 0;
+    long long iters = 0, Wbest = 0;
+    bool have = false;
+    leg_init<MT, NT, VPT, DV>(g, p, 0, msg, ws, Lam, bb, gg);
+    __syncthreads();
+    for (;;) {
+        uint32_t *pc = par + pb * g.m_words;
+        check_pass<NT, DC>(g, reinterpret_cast<MT *>(msg), sg, pc, C);
+        __syncthreads();
+        fault_pass<MT, NT, VPT, DV>(g, msg, fw, pc, Lam, bb, gg, C);
+        __syncthreads();
+        ++iters;
+        ++t;
+        pb ^= 1;
+        const bool conv = warp_converged(pc, sg, g.m_words);
+        const bool spent = p.max_iters > 0 && iters >= p.max_iters;
+        const bool leg_end = conv || spent || t == (leg == 0 ? p.T1 : p.T2);
+        if (!leg_end) continue;
+        if (conv) {
+            ++sols;
+            warp_weight<NT, VPT>(g, ws, Lam, s_Wpart);
+        }
+        const bool done = sols >= p.S || leg == p.R || spent;
+        if (!done) {
+            ++leg;
+            t = 0;
+            leg_init<MT, NT, VPT, DV>(g, p, leg, msg, ws, Lam, bb, gg);
+        }
+        __syncthreads();  // the weight and the next leg's initial messages are visible
+        if (conv) {
+            const long long W = total_weight<NT>(s_Wpart);
+            if (!have || W < Wbest) {
+                store_bits<NT>(cor, fw, g.cor_words);
+                have = true;
+                Wbest = W;
+            }
+        }
+        if (done) break;
+    }
+    if (!have) store_bits<NT>(cor, fw, g.cor_words);
+    if (tid == 0) {
+        if (out.legs) out.legs[shot] = leg + 1;
+        if (out.conv) out.conv[shot] = have ? 1 : 0;
+        if (out.iters) out.iters[shot] = (int32_t)iters;
+    }
+}
+
+// One block per shot at a time; shots come from a global counter.
 template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
 __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams p,
                                                    const uint64_t *__restrict__ syn, int B,
@@ -427,9 +486,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
     smem_layout(g, smem_raw, fw, sg, par, ws);
     __shared__ int s_shot;
     __shared__ long long s_Wpart[NT / 32];
-    const int tid = threadIdx.x;
-    const float C = p.clip;
-    block_setup<MT, NT, DC>(g, msg, fw, ws, C);
+    block_setup<MT, NT, DC>(g, msg, fw, ws, p.clip);
 
     float Lam[VPT], bb[VPT], gg[VPT];
 #pragma unroll
@@ -437,58 +494,72 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
 
     for (;;) {
         __syncthreads();  // the previous shot is done with shared memory and s_shot
-        if (tid == 0) s_shot = (int)atomicAdd(counter, 1u);
+        if (threadIdx.x == 0) s_shot = (int)atomicAdd(counter, 1u);
         __syncthreads();
         const int shot = s_shot;
         if (shot >= B) break;
-        load_syndrome<NT>(g, syn + (size_t)shot * g.syn_words, sg);
-        uint64_t *cor = out.corr + (size_t)shot * g.cor_words;
+        decode_shot<MT, NT, VPT, DC, DV>(g, p, shot, syn + (size_t)shot * g.syn_words,
+                                         out.corr + (size_t)shot * g.cor_words, out, msg, fw,
+                                         sg, par, ws, s_Wpart, Lam, bb, gg);
+    }
+}
 
-        int leg = 0, sols = 0, t = 0, pb = 0;
-        long long iters = 0, Wbest = 0;
-        bool have = false;
-        leg_init<MT, NT, VPT, DV>(g, p, 0, msg, ws, Lam, bb, gg);
+// Mixed batch: shot b belongs to code code_of_shot[b] of the table; syndromes and
+// corrections are rows of fixed strides.  A block re-initialises its shared state
+// (padding slots, priors) whenever it moves to a shot of another code.
+template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
+__global__ void __launch_bounds__(NT, MINB) fused_decode_multi(MultiTable tab,
+                                                         const int32_t *__restrict__ code_of_shot,
+                                                         const uint64_t *__restrict__ syn,
+                                                         int syn_stride, int cor_stride, int B,
+                                                         DecodeOut out, unsigned int *counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *msg = smem_raw;
+    __shared__ FusedGraph s_g;
+    __shared__ DevParams s_p;
+    __shared__ int s_shot, s_code;
+    __shared__ long long s_Wpart[NT / 32];
+    int cur = -1;
+
+    float Lam[VPT], bb[VPT], gg[VPT];
+#pragma unroll
+    for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
+
+    for (;;) {
         __syncthreads();
-        for (;;) {
-            uint32_t *pc = par + pb * g.m_words;
-            check_pass<NT, DC>(g, reinterpret_cast<MT *>(msg), sg, pc, C);
-            __syncthreads();
-            fault_pass<MT, NT, VPT, DV>(g, msg, fw, pc, Lam, bb, gg, C);
-            __syncthreads();
-            ++iters;
-            ++t;
-            pb ^= 1;
-            const bool conv = warp_converged(pc, sg, g.m_words);
-            const bool spent = p.max_iters > 0 && iters >= p.max_iters;
-            const bool leg_end = conv || spent || t == (leg == 0 ? p.T1 : p.T2);
-            if (!leg_end) continue;
-            if (conv) {
-                ++sols;
-                warp_weight<NT, VPT>(g, ws, Lam, s_Wpart);
+        if (threadIdx.x == 0) {
+            const int shot = (int)atomicAdd(counter, 1u);
+            s_shot = shot;
+            int c = shot < B ? code_of_shot[shot] : 0;
+            if (c < 0 || c >= tab.n) c = -1;  // invalid code id: the shot is skipped
+            s_code = c;
+            if (c >= 0 && c != cur) {
+                s_g = tab.g[c];
+                s_p = tab.p[c];
             }
-            const bool done = sols >= p.S || leg == p.R || spent;
-            if (!done) {
-                ++leg;
-                t = 0;
-                leg_init<MT, NT, VPT, DV>(g, p, leg, msg, ws, Lam, bb, gg);
-            }
-            __syncthreads();  // the weight and the next leg's initial messages are visible
-            if (conv) {
-                const long long W = total_weight<NT>(s_Wpart);
-                if (!have || W < Wbest) {
-                    store_bits<NT>(cor, fw, g.cor_words);
-                    have = true;
-                    Wbest = W;
-                }
-            }
-            if (done) break;
         }
-        if (!have) store_bits<NT>(cor, fw, g.cor_words);
-        if (tid == 0) {
-            if (out.legs) out.legs[shot] = leg + 1;
-            if (out.conv) out.conv[shot] = have ? 1 : 0;
-            if (out.iters) out.iters[shot] = (int32_t)iters;
+        __syncthreads();
+        const int shot = s_shot, code = s_code;
+        if (shot >= B) break;
+        if (code < 0) {  // not a code of the table: marked by iters = -1
+            if (threadIdx.x == 0) {
+                if (out.legs) out.legs[shot] = 0;
+                if (out.conv) out.conv[shot] = 0;
+                if (out.iters) out.iters[shot] = -1;
+            }
+            continue;
         }
+        uint32_t *fw, *sg, *par;
+        float *ws;
+        smem_layout(s_g, smem_raw, fw, sg, par, ws);
+        if (code != cur) {
+            block_setup<MT, NT, DC>(s_g, msg, fw, ws, s_p.clip);
+            cur = code;
+            __syncthreads();
+        }
+        decode_shot<MT, NT, VPT, DC, DV>(s_g, s_p, shot, syn + (size_t)shot * syn_stride,
+                                         out.corr + (size_t)shot * cor_stride, out, msg, fw, sg,
+                                         par, ws, s_Wpart, Lam, bb, gg);
     }
 }
 
@@ -549,6 +620,15 @@ cudaError_t launch_decode(dim3 grid, size_t smem, cudaStream_t st, const FusedGr
     return cudaGetLastError();
 }
 
+template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
+cudaError_t launch_multi(dim3 grid, size_t smem, cudaStream_t st, const MultiTable &tab,
+                         const int32_t *code_of_shot, const uint64_t *syn, int syn_stride,
+                         int cor_stride, int B, DecodeOut out, unsigned int *counter) {
+    fused_decode_multi<MT, NT, VPT, MINB, DC, DV><<<grid, NT, smem, st>>>(
+        tab, code_of_shot, syn, syn_stride, cor_stride, B, out, counter);
+    return cudaGetLastError();
+}
+
 template <typename MT, int NT, int VPT, int DC, int DV>
 cudaError_t launch_trace(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                          const DevParams &p, const uint64_t *syn, int B, int T, float *marg,
@@ -574,6 +654,8 @@ FusedKernel entry() {
     k.dv = QL_DV;
     k.decode_fn = (const void *)fused_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
     k.launch_decode = &launch_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
+    k.multi_fn = (const void *)fused_decode_multi<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
+    k.launch_multi = &launch_multi<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
     if constexpr (TRACE) {
         k.trace_fn = (const void *)fused_trace<MsgT, NT, VPT, QL_DC, QL_DV>;
         k.launch_trace = &launch_trace<MsgT, NT, VPT, QL_DC, QL_DV>;

@@ -26,6 +26,7 @@ QLDPC_KERNEL_BASELINE = 1
 QLDPC_KERNEL_FUSED = 2
 
 EXPORTED = ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
+            "qldpc_decode_batch_multi",
             "qldpc_decode_batch_host_static", "qldpc_trace_first_leg", "qldpc_get_info",
             "qldpc_destroy", "qldpc_status_string", "qldpc_last_error", "qldpc_soft_create",
             "qldpc_soft_workspace_bytes", "qldpc_soft_forward", "qldpc_soft_backward",
@@ -86,6 +87,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qldpc_decode_batch.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P]
     lib.qldpc_decode_batch_host.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
     lib.qldpc_decode_batch_host_static.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
+    lib.qldpc_decode_batch_multi.argtypes = [P, ctypes.c_int32, P, P, ctypes.c_int32,
+                                             ctypes.c_int64, P, ctypes.c_int32, P, P, P, P]
     lib.qldpc_trace_first_leg.argtypes = [P, P, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
     lib.qldpc_get_info.argtypes = [P, ctypes.POINTER(qldpc_info)]
     lib.qldpc_destroy.argtypes = [P]
@@ -103,6 +106,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qldpc_soft_destroy.argtypes = [P]
     lib.qldpc_soft_destroy.restype = None
     for name in ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
+                 "qldpc_decode_batch_multi",
                  "qldpc_decode_batch_host_static", "qldpc_trace_first_leg", "qldpc_get_info",
                  "qldpc_soft_create", "qldpc_soft_workspace_bytes", "qldpc_soft_forward",
                  "qldpc_soft_backward"):
@@ -150,6 +154,39 @@ def qldpc_decode_batch_host(h, syndromes_ptr, B, corrections_ptr, legs_ptr=None,
     _check(load_library().qldpc_decode_batch_host(h, syndromes_ptr, int(B), corrections_ptr,
                                                   legs_ptr, conv_ptr, iters_ptr),
            "qldpc_decode_batch_host")
+
+
+def qldpc_decode_batch_multi(handles, code_ptr, syn_ptr, syn_stride, B, cor_ptr, cor_stride,
+                             legs_ptr=None, conv_ptr=None, iters_ptr=None, stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    _check(load_library().qldpc_decode_batch_multi(arr, len(handles), code_ptr, syn_ptr,
+                                                   int(syn_stride), int(B), cor_ptr,
+                                                   int(cor_stride), legs_ptr, conv_ptr, iters_ptr,
+                                                   stream),
+           "qldpc_decode_batch_multi")
+
+
+def decode_mixed(decoders, code_of_shot, syndromes, stream=None):
+    """Mixed batch through one persistent launch.
+
+    decoders: list of RelayDecoder; code_of_shot: int32 CUDA tensor [B];
+    syndromes: int64 CUDA tensor [B, stride] (each row starts with its code's
+    ceil(M/64) words).  Returns (corrections [B, max ceil(N/64)], legs, converged, iters).
+    """
+    import torch
+    B = syndromes.shape[0]
+    cw = max(d.correction_words for d in decoders)
+    dev = syndromes.device
+    cor = torch.zeros((B, cw), dtype=torch.int64, device=dev)
+    legs = torch.empty(B, dtype=torch.int32, device=dev)
+    conv = torch.empty(B, dtype=torch.uint8, device=dev)
+    iters = torch.empty(B, dtype=torch.int32, device=dev)
+    st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    qldpc_decode_batch_multi([d.handle for d in decoders], ctypes.c_void_p(code_of_shot.data_ptr()),
+                             ctypes.c_void_p(syndromes.data_ptr()), syndromes.shape[1], B,
+                             ctypes.c_void_p(cor.data_ptr()), cw, ctypes.c_void_p(legs.data_ptr()),
+                             ctypes.c_void_p(conv.data_ptr()), ctypes.c_void_p(iters.data_ptr()), st)
+    return cor, legs, conv, iters
 
 
 def qldpc_decode_batch_host_static(h, syndromes_ptr, B, corrections_ptr, legs_ptr=None,
