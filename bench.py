@@ -38,6 +38,7 @@ METRIC = "Relay-BP syndromes/s on 1 GB300 (gross code, 12 rds) and % of roofline
 
 
 def make_inputs(n_shots: int, seed: int, first_shot: int = 0):
+    """The benchmark workload: gross T=12 detector model, shots first_shot.. of the stream."""
     P = phenomenological_dem(BB144, 12, 0.003)
     F = sample_faults(P.p, seed, n_shots, first_shot=first_shot)
     sig = syndromes_of(P.row_ptr, P.col_idx, F)
@@ -50,6 +51,27 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def shard_first_shot(rank: int, shots_per_rank: int) -> int:
+    """Weak scaling: rank r decodes shots [r*S, (r+1)*S) of the counter-based shot stream."""
+    return rank * shots_per_rank
+
+
+def reduce_max_ms(ms: float, ws: int, device) -> float:
+    """Slowest rank's step time (the only collective of the benchmark; none on the data path)."""
+    if ws == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(ws: int, shots_per_rank: int, ms: float) -> float:
+    """Whole-job syndromes/s: every rank's shots over the slowest rank's step time."""
+    return ws * shots_per_rank / (ms / 1e3)
 
 
 # ---------------------------------------------------------------------------------------
@@ -265,10 +287,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     # weak scaling: each rank decodes its own 10^5 shots (shard `rank` of the shot stream)
-    P, sig, gam = make_inputs(SHOTS, SEED)
-    if rank > 0:
-        F = sample_faults(P.p, SEED, SHOTS, first_shot=rank * SHOTS)
-        sig = syndromes_of(P.row_ptr, P.col_idx, F)
+    P, sig, gam = make_inputs(SHOTS, SEED, first_shot=shard_first_shot(rank, SHOTS))
     packed = pack_bits(sig)
     syn = torch.from_numpy(packed.view(np.int64)).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
@@ -288,16 +307,13 @@ def run_ours(args):
         times = timed_decode(dec, syn, out, args.steps, args.warmup, stream, flush)
         t_wall = time.perf_counter() - t_wall
     torch.cuda.synchronize()
-    ms = sum(times) / len(times)
+    ms = reduce_max_ms(sum(times) / len(times), ws, dev)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     iters = out[3].cpu().numpy().astype(np.int64)
     conv = out[2].cpu().numpy()
     total_iters = int(iters.sum())
-    value = ws * SHOTS / (ms / 1e3)
+    value = aggregate_rate(ws, SHOTS, ms)
 
     if rank != 0:
         dec.close()
