@@ -37,11 +37,21 @@ S_SOLUTIONS = 5
 METRIC = "Relay-BP syndromes/s on 1 GB300 (gross code, 12 rds) and % of roofline"
 
 
-def make_inputs(n_shots: int, seed: int, first_shot: int = 0):
-    """The benchmark workload: gross T=12 detector model, shots first_shot.. of the stream."""
+def make_inputs(n_shots: int, seed: int, first_shot: int = 0, device=None):
+    """The benchmark workload: gross T=12 detector model, shots first_shot.. of the stream.
+
+    With a CUDA device the same seeded stream is sampled there (bit-identical to the
+    host sampler) and the syndromes are returned on the host.
+    """
     P = phenomenological_dem(BB144, 12, 0.003)
-    F = sample_faults(P.p, seed, n_shots, first_shot=first_shot)
-    sig = syndromes_of(P.row_ptr, P.col_idx, F)
+    if device is not None:
+        from workloads.torch_sampling import sample_faults_t, syndromes_t
+        F = sample_faults_t(P.p, seed, n_shots, first_shot=first_shot, device=device)
+        sig = syndromes_t(P.H, F).cpu().numpy()
+        del F
+    else:
+        F = sample_faults(P.p, seed, n_shots, first_shot=first_shot)
+        sig = syndromes_of(P.row_ptr, P.col_idx, F)
     gam = gamma_table(P.N, 300, 0.125, -0.24, 0.66, seed)
     return P, sig, gam
 
@@ -248,8 +258,8 @@ def run_decode_only(args):
 
     from paper_2511_21660_gb300 import (QLDPC_KERNEL_BASELINE, QLDPC_KERNEL_FUSED,
                                         QLDPC_MSG_FP16, QLDPC_MSG_FP32, RelayConfig, RelayDecoder)
-    P, sig, gam = make_inputs(args.shots, SEED)
     dev = torch.device("cuda", 0)
+    P, sig, gam = make_inputs(args.shots, SEED, device=dev)
     syn = torch.from_numpy(pack_bits(sig).view(np.int64)).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -287,7 +297,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     # weak scaling: each rank decodes its own 10^5 shots (shard `rank` of the shot stream)
-    P, sig, gam = make_inputs(SHOTS, SEED, first_shot=shard_first_shot(rank, SHOTS))
+    P, sig, gam = make_inputs(SHOTS, SEED, first_shot=shard_first_shot(rank, SHOTS), device=dev)
     packed = pack_bits(sig)
     syn = torch.from_numpy(packed.view(np.int64)).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2

@@ -119,3 +119,18 @@ def test_gamma_table():
 def test_code_capacity_problem():
     P = code_capacity_dem(BB72, 0.05)
     assert (P.M, P.N, P.E) == (36, 72, 216)
+
+
+def test_torch_sampler_is_bit_identical_to_numpy_sampler():
+    torch = pytest.importorskip("torch")
+    from workloads.torch_sampling import pack_bits_t, sample_faults_t, syndromes_t
+    P = phenomenological_dem(BB72, 3, 0.02)
+    p = P.p.copy()
+    p[:5] = [0.5, 1e-9, 0.3, 0.0031, 0.25]
+    F = sample_faults(p, 7, 300, first_shot=1000)
+    Ft = sample_faults_t(p, 7, 300, first_shot=1000, chunk=128)
+    assert np.array_equal(Ft.numpy(), F)
+    s = syndromes_of(P.row_ptr, P.col_idx, F)
+    st = syndromes_t(P.H, Ft)
+    assert np.array_equal(st.numpy(), s)
+    assert np.array_equal(pack_bits_t(st).numpy().view(np.uint64), pack_bits(s))
