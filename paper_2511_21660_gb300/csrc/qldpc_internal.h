@@ -93,7 +93,7 @@ struct FusedKernel {
 // Shared memory of the fused kernels for a graph (bytes).
 inline size_t fused_smem_bytes(int msg_bytes, int f_words, int syn_words, int m_words, int N) {
     size_t msg = ((size_t)msg_bytes + 15) & ~(size_t)15;
-    return msg + 4 * (size_t)f_words + 8 * (size_t)syn_words + 8 * (size_t)m_words +
+    return msg + 8 * (size_t)f_words + 8 * (size_t)syn_words + 8 * (size_t)m_words +
            4 * (size_t)N + 64;
 }
 

@@ -175,12 +175,17 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, cons
             sx ^= __float_as_uint(v[k]);
         }
         sx &= 0x80000000u;
+        // magnitude of slot k: m2 if |nu_k| = m1 (the smallest), else m1; every other
+        // |nu_k| is >= m2, so on the bit patterns of these non-negative floats
+        // bits(mag) = bits(m1) + bits(m2) - min(bits(|nu_k|), bits(m2)), exactly.
+        const uint32_t b12 = __float_as_uint(m1) + __float_as_uint(m2);
+        const uint32_t b2 = __float_as_uint(m2);
         float o[DC];
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
-            const float mag = (fabsf(v[k]) <= m1) ? m2 : m1;
-            o[k] = __uint_as_float(__float_as_uint(mag) |
-                                   ((sx ^ __float_as_uint(v[k])) & 0x80000000u));
+            const uint32_t vb = __float_as_uint(v[k]);
+            const uint32_t mag = b12 - min(vb & 0x7fffffffu, b2);
+            o[k] = __uint_as_float(mag | ((sx ^ vb) & 0x80000000u));
         }
         if (deg < DC) {
             const int f = swz<DC>(i);
@@ -259,21 +264,37 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, con
 template <typename MT, int DV>
 __device__ __forceinline__ float fault_update(unsigned char *msg, const int (&sl)[DV], int deg,
                                               float lam, float C) {
+    // The clamp is the identity unless some value exceeds C in magnitude, so it is
+    // applied only then (same values either way).
     if (deg == 3) {
         const float mu0 = Msg<MT>::ld(msg, sl[0]), mu1 = Msg<MT>::ld(msg, sl[1]),
                     mu2 = Msg<MT>::ld(msg, sl[2]);
         const float s0 = __fadd_rn(lam, mu0), s01 = __fadd_rn(s0, mu1);
-        Msg<MT>::st(msg, sl[0], clampc(__fadd_rn(__fadd_rn(lam, mu1), mu2), C));
-        Msg<MT>::st(msg, sl[1], clampc(__fadd_rn(s0, mu2), C));
-        Msg<MT>::st(msg, sl[2], clampc(s01, C));
-        return clampc(__fadd_rn(s01, mu2), C);
+        float n0 = __fadd_rn(__fadd_rn(lam, mu1), mu2), n1 = __fadd_rn(s0, mu2), n2 = s01;
+        float L = __fadd_rn(s01, mu2);
+        if (fmaxf(fmaxf(fabsf(n0), fabsf(n1)), fmaxf(fabsf(n2), fabsf(L))) > C) {
+            n0 = clampc(n0, C);
+            n1 = clampc(n1, C);
+            n2 = clampc(n2, C);
+            L = clampc(L, C);
+        }
+        Msg<MT>::st(msg, sl[0], n0);
+        Msg<MT>::st(msg, sl[1], n1);
+        Msg<MT>::st(msg, sl[2], n2);
+        return L;
     }
     if (deg == 2) {
         const float mu0 = Msg<MT>::ld(msg, sl[0]), mu1 = Msg<MT>::ld(msg, sl[1]);
         const float s0 = __fadd_rn(lam, mu0);
-        Msg<MT>::st(msg, sl[0], clampc(__fadd_rn(lam, mu1), C));
-        Msg<MT>::st(msg, sl[1], clampc(s0, C));
-        return clampc(__fadd_rn(s0, mu1), C);
+        float n0 = __fadd_rn(lam, mu1), n1 = s0, L = __fadd_rn(s0, mu1);
+        if (fmaxf(fmaxf(fabsf(n0), fabsf(n1)), fabsf(L)) > C) {
+            n0 = clampc(n0, C);
+            n1 = clampc(n1, C);
+            L = clampc(L, C);
+        }
+        Msg<MT>::st(msg, sl[0], n0);
+        Msg<MT>::st(msg, sl[1], n1);
+        return L;
     }
     float mu[DV];
 #pragma unroll
@@ -310,23 +331,25 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *m
         const int j = threadIdx.x + r * NT;
         const bool valid = j < g.N;
         float L = 0.0f;
+        int deg = 0;
         if (valid) {
             const float lam = __fadd_rn(bb[r], __fmul_rn(gg[r], Lam[r]));
             int sl[DV];
-            const int deg = load_slots<DV>(g, j, sl);
+            deg = load_slots<DV>(g, j, sl);
             L = fault_update<MT, DV>(msg, sl, deg, lam, C);
             Lam[r] = L;
-            if (L < 0.0f) {
-                const int *ck = g.var_chk + (size_t)j * DV;
-                for (int k = 0; k < deg; ++k) {
-                    const int c = __ldg(ck + k);
-                    atomicXor(par + (c >> 5), 1u << (c & 31));
-                }
-            }
         }
-        const uint32_t bal = __ballot_sync(FULL, valid && L < 0.0f);
+        const bool dec = valid && L < 0.0f;
+        const uint32_t bal = __ballot_sync(FULL, dec);
         const int jb = threadIdx.x - lane + r * NT;
         if (lane == 0 && jb < g.N) fw[jb >> 5] = bal;
+        if (bal != 0u && dec) {  // decided faults are few: flip their checks' parity
+            const int *ck = g.var_chk + (size_t)j * DV;
+            for (int k = 0; k < deg; ++k) {
+                const int c = __ldg(ck + k);
+                atomicXor(par + (c >> 5), 1u << (c & 31));
+            }
+        }
     }
 }
 
@@ -370,17 +393,38 @@ __device__ __forceinline__ void store_bits(uint64_t *dst, const uint32_t *fw, in
         dst[q] = (uint64_t)fw[2 * q] | ((uint64_t)fw[2 * q + 1] << 32);
 }
 
-// Shared memory: messages [msg_bytes], decision bitmap fw [f_words], syndrome sg
-// [2*syn_words] (bits past M cleared), two parity buffers par [2][m_words], prior
-// LLRs ws [N] (read by the weight sum and by leg initialisation).
+// Kept solution: the output row and the shared copy used by warp_same_solution.
+template <int NT>
+__device__ __forceinline__ void keep_solution(uint64_t *dst, const uint32_t *fw, uint32_t *fb,
+                                              int words) {
+    for (int q = threadIdx.x; q < words; q += NT) {
+        const uint32_t lo = fw[2 * q], hi = fw[2 * q + 1];
+        fb[2 * q] = lo;
+        fb[2 * q + 1] = hi;
+        dst[q] = (uint64_t)lo | ((uint64_t)hi << 32);
+    }
+}
+
+// Shared memory: messages [msg_bytes], decision bitmap fw [f_words], kept solution
+// fb [f_words], syndrome sg [2*syn_words] (bits past M cleared), two parity buffers
+// par [2][m_words], prior LLRs ws [N] (read by the weight sum and leg initialisation).
 __device__ __forceinline__ void smem_layout(const FusedGraph &g, unsigned char *raw,
-                                            uint32_t *&fw, uint32_t *&sg, uint32_t *&par,
-                                            float *&ws) {
+                                            uint32_t *&fw, uint32_t *&fb, uint32_t *&sg,
+                                            uint32_t *&par, float *&ws) {
     const size_t mb = ((size_t)g.msg_bytes + 15) & ~(size_t)15;
     fw = reinterpret_cast<uint32_t *>(raw + mb);
-    sg = fw + g.f_words;
+    fb = fw + g.f_words;
+    sg = fb + g.f_words;
     par = sg + 2 * g.syn_words;
     ws = reinterpret_cast<float *>(par + 2 * g.m_words);
+}
+
+// Is the decision bitmap equal to the kept solution?  Each warp decides on its own.
+__device__ __forceinline__ bool warp_same_solution(const uint32_t *fw, const uint32_t *fb,
+                                                   int words) {
+    uint32_t diff = 0;
+    for (int q = threadIdx.x & 31; q < words; q += 32) diff |= fw[q] ^ fb[q];
+    return !__any_sync(FULL, diff != 0u);
 }
 
 // Padding slots of every check hold C for good (the check pass writes C back).
@@ -420,8 +464,9 @@ __device__ __forceinline__ void load_syndrome(const FusedGraph &g, const uint64_
 template <typename MT, int NT, int VPT, int DC, int DV>
 __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams &p, int shot,
                                             const uint64_t *sy, uint64_t *cor, DecodeOut out,
-                                            unsigned char *msg, uint32_t *fw, uint32_t *sg,
-                                            uint32_t *par, float *ws, long long *s_Wpart,
+                                            unsigned char *msg, uint32_t *fw, uint32_t *fb,
+                                            uint32_t *sg, uint32_t *par, float *ws,
+                                            long long *s_Wpart,
                                             float (&Lam)[VPT], float (&bb)[VPT],
                                             float (&gg)[VPT]) {
     const int tid = threadIdx.x;
@@ -445,10 +490,10 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
         const bool spent = p.max_iters > 0 && iters >= p.max_iters;
         const bool leg_end = conv || spent || t == (leg == 0 ? p.T1 : p.T2);
         if (!leg_end) continue;
-        if (conv) {
-            ++sols;
-            warp_weight<NT, VPT>(g, ws, Lam, s_Wpart);
-        }
+        // a solution equal to the kept one has its weight and cannot replace it
+        const bool fresh = conv && !(have && warp_same_solution(fw, fb, 2 * g.cor_words));
+        if (conv) ++sols;
+        if (fresh) warp_weight<NT, VPT>(g, ws, Lam, s_Wpart);
         const bool done = sols >= p.S || leg == p.R || spent;
         if (!done) {
             ++leg;
@@ -456,10 +501,10 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
             leg_init<MT, NT, VPT, DV>(g, p, leg, msg, ws, Lam, bb, gg);
         }
         __syncthreads();  // the weight and the next leg's initial messages are visible
-        if (conv) {
+        if (fresh) {
             const long long W = total_weight<NT>(s_Wpart);
             if (!have || W < Wbest) {
-                store_bits<NT>(cor, fw, g.cor_words);
+                keep_solution<NT>(cor, fw, fb, g.cor_words);
                 have = true;
                 Wbest = W;
             }
@@ -481,9 +526,9 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
                                                    DecodeOut out, unsigned int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *msg = smem_raw;
-    uint32_t *fw, *sg, *par;
+    uint32_t *fw, *fb, *sg, *par;
     float *ws;
-    smem_layout(g, smem_raw, fw, sg, par, ws);
+    smem_layout(g, smem_raw, fw, fb, sg, par, ws);
     __shared__ int s_shot;
     __shared__ long long s_Wpart[NT / 32];
     block_setup<MT, NT, DC>(g, msg, fw, ws, p.clip);
@@ -500,7 +545,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
         if (shot >= B) break;
         decode_shot<MT, NT, VPT, DC, DV>(g, p, shot, syn + (size_t)shot * g.syn_words,
                                          out.corr + (size_t)shot * g.cor_words, out, msg, fw,
-                                         sg, par, ws, s_Wpart, Lam, bb, gg);
+                                         fb, sg, par, ws, s_Wpart, Lam, bb, gg);
     }
 }
 
@@ -549,17 +594,17 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode_multi(MultiTable tab,
             }
             continue;
         }
-        uint32_t *fw, *sg, *par;
+        uint32_t *fw, *fb, *sg, *par;
         float *ws;
-        smem_layout(s_g, smem_raw, fw, sg, par, ws);
+        smem_layout(s_g, smem_raw, fw, fb, sg, par, ws);
         if (code != cur) {
             block_setup<MT, NT, DC>(s_g, msg, fw, ws, s_p.clip);
             cur = code;
             __syncthreads();
         }
         decode_shot<MT, NT, VPT, DC, DV>(s_g, s_p, shot, syn + (size_t)shot * syn_stride,
-                                         out.corr + (size_t)shot * cor_stride, out, msg, fw, sg,
-                                         par, ws, s_Wpart, Lam, bb, gg);
+                                         out.corr + (size_t)shot * cor_stride, out, msg, fw, fb,
+                                         sg, par, ws, s_Wpart, Lam, bb, gg);
     }
 }
 
@@ -570,9 +615,9 @@ __global__ void __launch_bounds__(NT) fused_trace(FusedGraph g, DevParams p,
                                                   int E, float *marg, float *nu, float *mu) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *msg = smem_raw;
-    uint32_t *fw, *sg, *par;
+    uint32_t *fw, *fb, *sg, *par;
     float *ws;
-    smem_layout(g, smem_raw, fw, sg, par, ws);
+    smem_layout(g, smem_raw, fw, fb, sg, par, ws);
     const int shot = blockIdx.x;
     const float C = p.clip;
     block_setup<MT, NT, DC>(g, msg, fw, ws, C);
@@ -683,7 +728,10 @@ void QL_EXPAND(QL_P, QL_DC, QL_DV)(const FusedKernel **out, int *n) {
     static const FusedKernel table[] = {
         entry<256, 4, 4, false>(),
         entry<512, 6, 2, false>(),
-        entry<256, 12, 3, false>(),
+        entry<256, 12, 4, false>(),
+        entry<384, 8, 3, false>(),
+        entry<640, 5, 2, false>(),
+        entry<768, 4, 2, false>(),
         entry<512, 16, 1, false>(),
         entry<512, 32, 1, true>(),
     };
