@@ -237,6 +237,51 @@ int qldpc_soft_backward(qldpc_soft *s, const uint64_t *syndromes, const uint64_t
 /* Free the soft handle (syncs through cudaFree).  NULL is ignored. */
 void qldpc_soft_destroy(qldpc_soft *s);
 
+/* ---- Filtered-OSD post-processor (paper Sec. 5, pre-decoder set-up of Sec. 7.1) ----
+ *
+ * For each shot not marked in `skip` (typically the shots whose first Relay leg did
+ * not converge; the paper's pre-decoder is that leg, T_1 = 80 with gamma_0):
+ *   1. bp_iters iterations of plain min-sum BP (Sec. 2.3, "Belief propagation
+ *      decoding") from the priors, no early exit, give the marginals Lambda;
+ *   2. R = the faults with Lambda_j < llr_confident (a float32 compare), sorted by
+ *      increasing Lambda_j, ties by increasing j; |R| > max_candidates fails;
+ *   3. x solves H_R x = sigma with x supported on the leftmost linearly independent
+ *      columns of H_R (free columns 0), found by the streaming ("lifted") Gauss-Jordan
+ *      elimination of Sec. 4; no solution fails;
+ *   4. F_j = x_r for j = R_r.
+ * The paper fixes bp_iters = 25 and |R|_max = 500 (Sec. 7.1, App. on the OSD design);
+ * it gives no value for Lambda_confident. */
+typedef struct qldpc_osd qldpc_osd;
+
+typedef struct {
+    int32_t bp_iters;        /* >= 0 plain BP iterations before the ranking (paper 25)        */
+    float llr_confident;     /* finite; keep faults with Lambda_j < llr_confident              */
+    int32_t max_candidates;  /* |R|_max, 1..1024 (paper 500)                                   */
+} qldpc_osd_params;
+
+#define QLDPC_OSD_SKIPPED 0        /* skip[b] != 0: nothing written                           */
+#define QLDPC_OSD_SOLVED 1         /* corrections[b] holds the OSD correction                 */
+#define QLDPC_OSD_TOO_MANY (-1)    /* |R| > max_candidates; corrections[b] untouched          */
+#define QLDPC_OSD_NO_SOLUTION (-2) /* H_R x = sigma has no solution; corrections[b] untouched */
+
+/* Copy H (CSR as in qldpc_create, N <= 32767, check degree <= 32, fault degree <= 8)
+ * and the priors to `device`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
+int qldpc_osd_create(qldpc_osd **out, int32_t M, int32_t N, const int32_t *row_ptr,
+                     const int32_t *col_idx, const double *priors,
+                     const qldpc_osd_params *params, int device);
+
+/* Post-process B shots (device pointers): syndromes [B][ceil(M/64)] u64; skip [B] u8
+ * or NULL (post-process every shot); corrections [B][ceil(N/64)] u64, written only for
+ * solved shots (pass the pre-decoder's corrections to keep them elsewhere); status [B]
+ * int32 (QLDPC_OSD_*); n_candidates [B] int32 |R| or NULL.  Asynchronous on `stream`
+ * (cudaStream_t, NULL = legacy default stream).  Errors: INVALID_ARG, CUDA. */
+int qldpc_osd_decode_batch(qldpc_osd *o, const uint64_t *syndromes, int64_t B,
+                           const uint8_t *skip, uint64_t *corrections, int32_t *status,
+                           int32_t *n_candidates, void *stream);
+
+/* Wait for the handle's work, then free it.  NULL is ignored. */
+void qldpc_osd_destroy(qldpc_osd *o);
+
 /* Fill *info.  Errors: INVALID_ARG. */
 int qldpc_get_info(const qldpc_decoder *d, qldpc_info *info);
 

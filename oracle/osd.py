@@ -106,6 +106,12 @@ def filtered_osd(H: np.ndarray, sigma: np.ndarray, llr: np.ndarray, prm: OSDPara
 def bp_llrs(row_ptr, col_idx, priors, sigma, T: int = 25, precision: str = "f32"):
     """Marginals after T iterations of min-sum BP (gamma = 0), no early exit."""
     N = np.asarray(priors).size
+    if T == 0:                               # no iteration: the prior LLRs themselves
+        p = np.asarray(priors, dtype=np.float64)
+        w = np.log((1.0 - p) / p)
+        if precision != "f64":
+            w = w.astype(np.float32).astype(np.float64)
+        return np.repeat(w[None, :], np.asarray(sigma).shape[0], axis=0)
     Lam, _, _ = dmem_trace(row_ptr, col_idx, priors, np.zeros(N), sigma, T,
                            precision=precision, want_messages=False)
     return Lam[:, T - 1, :]

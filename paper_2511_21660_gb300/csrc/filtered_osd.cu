@@ -1,0 +1,282 @@
+// Filtered-OSD post-processor (paper Sec. 5, "Filtered ordered statistics decoding",
+// with the pre-decoder set-up of Sec. 7.1), one thread block per shot at a time:
+//
+//   1. plain min-sum BP (Sec. 2.3, "Belief propagation decoding") for bp_iters
+//      iterations from the priors: the Relay check and fault passes with every
+//      gamma_j = 0, no early exit; Lambda stays in registers;
+//   2. filtered ranking (Sec. 5, "Filtered column ranking"): the faults with
+//      Lambda_j < llr_conf are compacted by warp ballots and sorted by (Lambda_j, j)
+//      with a bitonic network in shared memory; more than max_cand is a failure;
+//   3. submatrix (Sec. 5, "Extracting submatrix and filtering out zero rows"): the
+//      checks touched by R are marked; an untouched check with sigma_i = 1 makes the
+//      system unsolvable; only touched rows are streamed;
+//   4. solver (Sec. 4, Algorithm "Lifted Gauss-Jordan over F_2", as the paper's
+//      systolic solver applies it): one warp streams the touched rows in check order;
+//      a row is reduced by locked pivot rows until its leftmost 1 (in ranking order)
+//      is an unlocked column, where it is stored with its syndrome bit; a row reduced
+//      to zero with syndrome bit 1 means no solution.  Back substitution over the
+//      locked columns, from the right, gives x with free columns 0;
+//   5. F_j = x_r for j = R_r (Sec. 5, "Algorithm output").
+//
+// A pivot row is a W-word bitset over ranking positions held by lanes 0..W-1 (lane l
+// owns word l), so the reduction of a row by a pivot row is one 32-bit XOR per lane.
+#include "relay_device.cuh"
+
+namespace qldpc {
+namespace {
+
+// Order-preserving map of a float (not NaN, not -0) onto uint32.
+__device__ __forceinline__ uint32_t sortable(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+template <int NT>
+__device__ __forceinline__ void bitonic_sort(uint64_t *keys, int n) {
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < n; i += NT) {
+                const int ixj = i ^ jj;
+                if (ixj > i) {
+                    const uint64_t a = keys[i], b = keys[ixj];
+                    const bool ascending = (i & k) == 0;
+                    if ((a > b) == ascending) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int NT, int VPT, int DC, int DV>
+__global__ void __launch_bounds__(NT, 1) osd_decode(FusedGraph g, DevParams p, OsdArgs o,
+                                                    const uint64_t *__restrict__ syn,
+                                                    const uint8_t *__restrict__ skip, int B,
+                                                    OsdOut out, unsigned int *counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *msg = smem_raw;
+    uint64_t *keys = reinterpret_cast<uint64_t *>(smem_raw);
+    uint32_t *up = reinterpret_cast<uint32_t *>(smem_raw + 8 * (size_t)o.KP);
+    int16_t *pos = reinterpret_cast<int16_t *>(smem_raw + 8 * (size_t)o.KP +
+                                               4 * (size_t)o.max_cand * o.W);
+    uint32_t *fw = reinterpret_cast<uint32_t *>(smem_raw + osd_union_bytes(g, o));
+    uint32_t *fb = fw + g.f_words;
+    uint32_t *sg = fb + g.f_words;
+    uint32_t *par = sg + 2 * g.syn_words;
+    float *ws = reinterpret_cast<float *>(par + 2 * g.m_words);
+    __shared__ int s_shot, s_cnt, s_bad;
+    __shared__ uint32_t s_x[32];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const float C = p.clip;
+
+    float Lam[VPT], bb[VPT], gg[VPT];
+#pragma unroll
+    for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
+
+    for (;;) {
+        __syncthreads();  // the previous shot is done with shared memory
+        if (tid == 0) s_shot = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int shot = s_shot;
+        if (shot >= B) break;
+        if (skip && skip[shot]) {
+            if (tid == 0) {
+                out.status[shot] = 0;
+                if (out.ncand) out.ncand[shot] = 0;
+            }
+            continue;
+        }
+
+        // 1. plain BP: lambda_j(t) = w_j (gamma row of zeros), Lambda from the priors
+        block_setup<float, NT, DC>(g, msg, fw, ws, C);
+        load_syndrome<NT>(g, syn + (size_t)shot * g.syn_words, sg);
+        if (tid == 0) {
+            s_cnt = 0;
+            s_bad = 0;
+        }
+        __syncthreads();
+        leg_init<float, NT, VPT, DV>(g, p, 0, msg, ws, Lam, bb, gg);
+        __syncthreads();
+        for (int t = 0; t < o.bp_iters; ++t) {
+            check_pass<NT, DC>(g, reinterpret_cast<float *>(msg), sg, par, C);
+            __syncthreads();
+            fault_pass<float, NT, VPT, DV>(g, msg, fw, par, Lam, bb, gg, C);
+            __syncthreads();
+        }
+
+        // 2. ranking: candidates Lambda_j < llr_conf, keys (Lambda_j, j)
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) {
+            const int j = tid + r * NT;
+            const bool valid = j < g.N;
+            const float x = valid ? canon(Lam[r]) : 0.0f;
+            const bool cand = valid && x < o.llr_conf;
+            const uint32_t bal = __ballot_sync(FULL, cand);
+            if (bal) {
+                const int leader = __ffs(bal) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&s_cnt, __popc(bal));
+                base = __shfl_sync(FULL, base, leader);
+                if (cand) {
+                    const int idx = base + __popc(bal & ((1u << lane) - 1u));
+                    if (idx < o.KP) keys[idx] = ((uint64_t)sortable(x) << 32) | (uint32_t)j;
+                }
+            }
+        }
+        __syncthreads();
+        const int n = s_cnt;
+        if (n > o.max_cand) {
+            if (tid == 0) {
+                out.status[shot] = -1;
+                if (out.ncand) out.ncand[shot] = n;
+            }
+            continue;
+        }
+        int np2 = 1;
+        while (np2 < n) np2 <<= 1;
+        for (int q = n + tid; q < np2; q += NT) keys[q] = ~0ull;
+        __syncthreads();
+        bitonic_sort<NT>(keys, np2);
+
+        // 3. inverse ranking and the checks touched by R (par reused as the bitmap)
+        for (int j = tid; j < g.N; j += NT) pos[j] = -1;
+        for (int q = tid; q < g.m_words; q += NT) par[q] = 0u;
+        __syncthreads();
+        for (int r = tid; r < n; r += NT) {
+            const int j = (int)(uint32_t)keys[r];
+            pos[j] = (int16_t)r;
+            const int deg = (int)((uint32_t)__ldg(g.var_slot + (size_t)j * DV) >> 24);
+            for (int k = 0; k < deg; ++k) {
+                const int c = __ldg(g.var_chk + (size_t)j * DV + k);
+                atomicOr(par + (c >> 5), 1u << (c & 31));
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < g.m_words; q += NT)
+            if (sg[q] & ~par[q]) s_bad = 1;  // a syndrome bit on a row H_R leaves empty
+        __syncthreads();
+
+        // 4. lifted elimination and back substitution by warp 0
+        if (tid < 32 && !s_bad) {
+            uint32_t lockw = 0u, specw = 0u;  // lane l: locked / syndrome bits of word l
+            bool bad = false;
+            for (int w = 0; w < g.m_words && !bad; ++w) {
+                uint32_t tw = par[w];
+                while (tw) {
+                    const int c = 32 * w + __ffs(tw) - 1;
+                    tw &= tw - 1u;
+                    int pr = -1;
+                    if (lane < DC) {
+                        const int jv = __ldg(o.chk_var + (size_t)c * DC + lane);
+                        if (jv >= 0) pr = pos[jv];
+                    }
+                    uint32_t row = 0u;
+#pragma unroll
+                    for (int s = 0; s < DC; ++s) {
+                        const int ps = __shfl_sync(FULL, pr, s);
+                        if (ps >= 0 && (ps >> 5) == lane) row |= 1u << (ps & 31);
+                    }
+                    uint32_t spec = (sg[c >> 5] >> (c & 31)) & 1u;
+                    // each reduction clears the row's leading column, so at most n + 1 steps
+                    for (int step = 0; step <= n; ++step) {
+                        const uint32_t nz = __ballot_sync(FULL, row != 0u);
+                        if (nz == 0u) {
+                            bad = spec != 0u;
+                            break;
+                        }
+                        const int wl = __ffs(nz) - 1;
+                        const int bit = __ffs(__shfl_sync(FULL, row, wl)) - 1;
+                        const int pc = 32 * wl + bit;
+                        const uint32_t lk = __shfl_sync(FULL, lockw, wl);
+                        if ((lk >> bit) & 1u) {
+                            if (lane < o.W) row ^= up[(size_t)pc * o.W + lane];
+                            spec ^= (__shfl_sync(FULL, specw, wl) >> bit) & 1u;
+                        } else {
+                            if (lane < o.W) up[(size_t)pc * o.W + lane] = row;
+                            if (lane == wl) {
+                                lockw |= 1u << bit;
+                                specw |= spec << bit;
+                            }
+                            break;
+                        }
+                    }
+                    if (bad) break;
+                }
+            }
+            uint32_t xw = 0u;
+            if (!bad) {
+                for (int pc = n - 1; pc >= 0; --pc) {
+                    const int wl = pc >> 5, bit = pc & 31;
+                    if (!((__shfl_sync(FULL, lockw, wl) >> bit) & 1u)) continue;
+                    const uint32_t t = lane < o.W ? (up[(size_t)pc * o.W + lane] & xw) : 0u;
+                    const uint32_t parity = __popc(__ballot_sync(FULL, __popc(t) & 1u)) & 1u;
+                    const uint32_t xp = ((__shfl_sync(FULL, specw, wl) >> bit) & 1u) ^ parity;
+                    if (xp && lane == wl) xw |= 1u << bit;
+                }
+            }
+            s_x[lane] = xw;
+            if (lane == 0 && bad) s_bad = 1;
+        }
+        __syncthreads();
+
+        // 5. scatter x to the faults of R
+        if (s_bad) {
+            if (tid == 0) {
+                out.status[shot] = -2;
+                if (out.ncand) out.ncand[shot] = n;
+            }
+            continue;
+        }
+        for (int q = tid; q < 2 * g.cor_words; q += NT) fw[q] = 0u;
+        __syncthreads();
+        for (int r = tid; r < n; r += NT)
+            if ((s_x[r >> 5] >> (r & 31)) & 1u) {
+                const int j = (int)(uint32_t)keys[r];
+                atomicOr(fw + (j >> 5), 1u << (j & 31));
+            }
+        __syncthreads();
+        store_bits<NT>(out.corr + (size_t)shot * g.cor_words, fw, g.cor_words);
+        if (tid == 0) {
+            out.status[shot] = 1;
+            if (out.ncand) out.ncand[shot] = n;
+        }
+    }
+}
+
+template <int NT, int VPT, int DC, int DV>
+cudaError_t launch_osd(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
+                       const DevParams &p, const OsdArgs &o, const uint64_t *syn,
+                       const uint8_t *skip, int B, OsdOut out, unsigned int *counter) {
+    osd_decode<NT, VPT, DC, DV><<<grid, NT, smem, st>>>(g, p, o, syn, skip, B, out, counter);
+    return cudaGetLastError();
+}
+
+template <int NT, int VPT, int DC, int DV>
+OsdKernel osd_entry() {
+    OsdKernel k;
+    k.threads = NT;
+    k.vpt = VPT;
+    k.dc = DC;
+    k.dv = DV;
+    k.fn = (const void *)osd_decode<NT, VPT, DC, DV>;
+    k.launch = &launch_osd<NT, VPT, DC, DV>;
+    return k;
+}
+
+}  // namespace
+
+void osd_table(const OsdKernel **out, int *n) {
+    // per (DC, DV) family of the fused layout: the first entry with threads * vpt >= N
+    static const OsdKernel table[] = {
+        osd_entry<512, 8, 8, 4>(),  osd_entry<512, 16, 8, 4>(),
+        osd_entry<512, 8, 16, 8>(), osd_entry<512, 16, 16, 8>(),
+        osd_entry<512, 8, 32, 8>(), osd_entry<512, 16, 32, 8>(),
+    };
+    *out = table;
+    *n = (int)(sizeof(table) / sizeof(table[0]));
+}
+
+}  // namespace qldpc

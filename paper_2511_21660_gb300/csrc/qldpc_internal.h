@@ -97,6 +97,43 @@ inline size_t fused_smem_bytes(int msg_bytes, int f_words, int syn_words, int m_
            4 * (size_t)N + 64;
 }
 
+// Filtered-OSD post-processor (paper Sec. 5): plain min-sum BP on the fused layout
+// (the graph's gamma row is all zeros), then ranking, submatrix and GF(2) solve.
+constexpr int kOsdMaxCandidates = 1024;
+struct OsdArgs {
+    const int32_t *chk_var;  // [Mp][DC] fault of the k-th edge of check i, -1 past its degree
+    int bp_iters;            // plain BP iterations before the ranking
+    float llr_conf;          // keep faults with Lambda_j < llr_conf
+    int max_cand;            // |R|_max, 1..kOsdMaxCandidates
+    int W;                   // 32-bit words of a pivot row: ceil(max_cand / 32)
+    int KP;                  // sort capacity: the power of two >= max_cand
+};
+struct OsdOut {
+    uint64_t *corr;    // [B][cor_words], written for solved shots only
+    int32_t *status;   // [B] 0 skipped, 1 solved, -1 too many candidates, -2 no solution
+    int32_t *ncand;    // [B] |R| (may be NULL)
+};
+struct OsdKernel {
+    int threads, vpt, dc, dv;
+    const void *fn;
+    cudaError_t (*launch)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
+                          const DevParams &p, const OsdArgs &o, const uint64_t *syn,
+                          const uint8_t *skip, int B, OsdOut out, unsigned int *counter);
+};
+void osd_table(const OsdKernel **out, int *n);
+// The OSD stage reuses the message area: keys [KP] u64, pivot rows [max_cand][W] u32,
+// the inverse ranking [N] i16.
+__host__ __device__ inline size_t osd_union_bytes(const FusedGraph &g, const OsdArgs &o) {
+    const size_t msg = ((size_t)g.msg_bytes + 15) & ~(size_t)15;
+    const size_t osd = 8 * (size_t)o.KP + 4 * (size_t)o.max_cand * o.W + 2 * (size_t)g.N;
+    const size_t u = msg > osd ? msg : osd;
+    return (u + 15) & ~(size_t)15;
+}
+inline size_t osd_smem_bytes(const FusedGraph &g, const OsdArgs &o) {
+    return osd_union_bytes(g, o) + 8 * (size_t)g.f_words + 8 * (size_t)g.syn_words +
+           8 * (size_t)g.m_words + 4 * (size_t)g.N + 64;
+}
+
 // Tables of compiled fused kernels, one per (precision, DC, DV) translation unit.
 #define QLDPC_DECLARE_TABLE(P, DC, DV) \
     void fused_table_##P##_##DC##_##DV(const FusedKernel **out, int *n);

@@ -30,7 +30,12 @@ EXPORTED = ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
             "qldpc_decode_batch_host_static", "qldpc_trace_first_leg", "qldpc_get_info",
             "qldpc_destroy", "qldpc_status_string", "qldpc_last_error", "qldpc_soft_create",
             "qldpc_soft_workspace_bytes", "qldpc_soft_forward", "qldpc_soft_backward",
-            "qldpc_soft_destroy")
+            "qldpc_soft_destroy", "qldpc_osd_create", "qldpc_osd_decode_batch",
+            "qldpc_osd_destroy")
+QLDPC_OSD_SKIPPED = 0
+QLDPC_OSD_SOLVED = 1
+QLDPC_OSD_TOO_MANY = -1
+QLDPC_OSD_NO_SOLUTION = -2
 QLDPC_REAL_FP32 = 0
 QLDPC_REAL_FP64 = 1
 QLDPC_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
@@ -50,6 +55,11 @@ class qldpc_relay_params(ctypes.Structure):
         ("llr_clip", ctypes.c_float),
         ("gamma_table", ctypes.c_void_p),
     ]
+
+
+class qldpc_osd_params(ctypes.Structure):
+    _fields_ = [("bp_iters", ctypes.c_int32), ("llr_confident", ctypes.c_float),
+                ("max_candidates", ctypes.c_int32)]
 
 
 class qldpc_info(ctypes.Structure):
@@ -97,6 +107,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qldpc_status_string.restype = ctypes.c_char_p
     lib.qldpc_last_error.argtypes = []
     lib.qldpc_last_error.restype = ctypes.c_char_p
+    lib.qldpc_osd_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, P, P, P,
+                                     ctypes.POINTER(qldpc_osd_params), ctypes.c_int]
+    lib.qldpc_osd_decode_batch.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P]
+    lib.qldpc_osd_destroy.argtypes = [P]
+    lib.qldpc_osd_destroy.restype = None
     lib.qldpc_soft_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, P, P, P,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]
     lib.qldpc_soft_workspace_bytes.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
@@ -481,3 +496,92 @@ class _Lazy:
 
 
 _SoftDMemLoss = _Lazy()
+
+
+# ---- filtered-OSD post-processor -----------------------------------------------------
+
+def qldpc_osd_create(M, N, row_ptr, col_idx, priors, params: qldpc_osd_params, device=0):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    pr = np.ascontiguousarray(priors, dtype=np.float64)
+    _check(lib.qldpc_osd_create(ctypes.byref(h), int(M), int(N), rp.ctypes.data, ci.ctypes.data,
+                                pr.ctypes.data, ctypes.byref(params), int(device)),
+           "qldpc_osd_create")
+    return h
+
+
+def qldpc_osd_decode_batch(h, syn_ptr, B, skip_ptr, cor_ptr, status_ptr, ncand_ptr=None,
+                           stream=None):
+    _check(load_library().qldpc_osd_decode_batch(h, syn_ptr, int(B), skip_ptr, cor_ptr,
+                                                 status_ptr, ncand_ptr, stream),
+           "qldpc_osd_decode_batch")
+
+
+def qldpc_osd_destroy(h) -> None:
+    if h is not None and h.value:
+        load_library().qldpc_osd_destroy(h)
+
+
+class FilteredOSD:
+    """Filtered-OSD post-processor for one decoding problem on one GPU (paper Sec. 5)."""
+
+    def __init__(self, row_ptr, col_idx, priors, bp_iters: int = 25,
+                 llr_confident: float = 8.0, max_candidates: int = 500, device: int = 0):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        self.M = row_ptr.size - 1
+        self.N = int(np.asarray(priors).size)
+        self.params = qldpc_osd_params(bp_iters, llr_confident, max_candidates)
+        self.device = device
+        self.handle = qldpc_osd_create(self.M, self.N, row_ptr, col_idx, priors, self.params,
+                                       device)
+        self.syndrome_words = (self.M + 63) // 64
+        self.correction_words = (self.N + 63) // 64
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            qldpc_osd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, syndromes, corrections, skip=None, status=None, n_candidates=None,
+               stream=None):
+        """Post-process the shots with skip == 0 (all shots when skip is None).
+
+        syndromes int64 [B, ceil(M/64)] and corrections int64 [B, ceil(N/64)] (updated in
+        place for solved shots) are CUDA tensors; returns (status int32 [B],
+        n_candidates int32 [B]).
+        """
+        import torch
+        B = syndromes.shape[0]
+        if syndromes.shape != (B, self.syndrome_words) or not syndromes.is_contiguous():
+            raise ValueError("syndromes must be a contiguous CUDA tensor [B, ceil(M/64)]")
+        if corrections.shape != (B, self.correction_words) or not corrections.is_contiguous():
+            raise ValueError("corrections must be a contiguous CUDA tensor [B, ceil(N/64)]")
+        dev = syndromes.device
+        status = status if status is not None else torch.empty(B, dtype=torch.int32, device=dev)
+        ncand = n_candidates if n_candidates is not None else torch.empty(B, dtype=torch.int32,
+                                                                          device=dev)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        qldpc_osd_decode_batch(self.handle, ctypes.c_void_p(syndromes.data_ptr()), B,
+                               _vp(skip) if skip is not None else None,
+                               ctypes.c_void_p(corrections.data_ptr()),
+                               ctypes.c_void_p(status.data_ptr()),
+                               ctypes.c_void_p(ncand.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+        return status, ncand
+
+
+def first_leg_then_osd(first_leg: "RelayDecoder", osd: FilteredOSD, syndromes, stream=None):
+    """The post-processed decoder of the paper's comparison (Sec. 7.1): the first Relay
+    leg (a RelayDecoder with legs_after_first = 0) on every shot, filtered-OSD on the
+    shots it leaves unconverged.  Returns (corrections, status, n_candidates, converged)
+    with status QLDPC_OSD_SKIPPED where the first leg converged."""
+    cor, _, conv, _ = first_leg.decode(syndromes, stream=stream)
+    status, ncand = osd.decode(syndromes, cor, skip=conv, stream=stream)
+    return cor, status, ncand, conv

@@ -1,0 +1,135 @@
+"""Parity of the CUDA filtered-OSD post-processor (through the C ABI) with the oracle.
+
+The plain-BP marginals are float32 on both sides (the oracle's single-precision
+mirror), so the ranking, and with it the GF(2) system and its solution, must match bit
+for bit: status, |R| and the correction of every shot.
+"""
+import numpy as np
+import pytest
+
+from oracle.osd import OSDParams, bp_llrs, filtered_osd, first_leg_then_osd as oracle_pipeline
+from workloads import (BB72, BB144, BB288, gamma_table, pack_bits, phenomenological_dem,
+                       sample_faults, syndromes_of, unpack_bits)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+from paper_2511_21660_gb300 import (FilteredOSD, QLDPC_OSD_SKIPPED, QLDPC_OSD_SOLVED,  # noqa: E402
+                                    RelayConfig, RelayDecoder, first_leg_then_osd)
+
+STATUS = {1: QLDPC_OSD_SOLVED, -1: -1, -2: -2}
+
+
+def _shots(P, n, seed):
+    F = sample_faults(P.p, seed, n)
+    return F, syndromes_of(P.row_ptr, P.col_idx, F)
+
+
+def _gpu_osd(P, sig, prm, skip=None, init=None):
+    osd = FilteredOSD(P.row_ptr, P.col_idx, P.p, prm.bp_iters, prm.llr_confident,
+                      prm.max_candidates)
+    try:
+        syn = torch.from_numpy(pack_bits(sig).view(np.int64)).cuda()
+        B = sig.shape[0]
+        cor = (torch.from_numpy(pack_bits(init).view(np.int64)).cuda() if init is not None
+               else torch.zeros((B, osd.correction_words), dtype=torch.int64, device="cuda"))
+        sk = torch.from_numpy(skip.astype(np.uint8)).cuda() if skip is not None else None
+        st, nc = osd.decode(syn, cor, skip=sk)
+        torch.cuda.synchronize()
+        return (unpack_bits(cor.cpu().numpy().view(np.uint64), P.N), st.cpu().numpy(),
+                nc.cpu().numpy())
+    finally:
+        osd.close()
+
+
+def _oracle_osd(P, sig, prm):
+    L = bp_llrs(P.row_ptr, P.col_idx, P.p, sig, prm.bp_iters, precision="f32")
+    out = [filtered_osd(P.H, sig[b], L[b], prm) for b in range(sig.shape[0])]
+    return (np.array([o[0] for o in out]), np.array([o[1] for o in out]),
+            np.array([o[2] for o in out]))
+
+
+def _assert_same(got, ref, label):
+    cor, st, nc = got
+    rcor, rst, rnc = ref
+    assert (st == rst).all(), (label, np.nonzero(st != rst)[0][:5], st[st != rst][:5],
+                               rst[st != rst][:5])
+    assert (nc == rnc).all(), (label, nc[nc != rnc][:5], rnc[nc != rnc][:5])
+    ok = st == QLDPC_OSD_SOLVED
+    assert (cor[ok] == rcor[ok]).all(), (label, np.nonzero((cor[ok] != rcor[ok]).any(1))[0][:5])
+
+
+# (code, rounds, p, shots, llr_confident, max_candidates): the 512-thread kernel with 8
+# faults per thread (N = 720, 2736) and with 16 (N = 8064); |R|_max 500 and 1024
+CASES = [(BB72, 6, 0.04, 300, 4.0, 500),
+         (BB144, 12, 0.02, 300, 8.0, 500),
+         (BB144, 12, 0.02, 120, 12.0, 1024),
+         (BB288, 18, 0.012, 60, 10.0, 500)]
+
+
+@pytest.mark.parametrize("code,T,p,n,conf,rmax", CASES)
+def test_osd_matches_oracle_on_every_shot(code, T, p, n, conf, rmax):
+    P = phenomenological_dem(code, T, p)
+    F, sig = _shots(P, n, 11)
+    prm = OSDParams(bp_iters=25, llr_confident=conf, max_candidates=rmax)
+    got = _gpu_osd(P, sig, prm)
+    ref = _oracle_osd(P, sig, prm)
+    _assert_same(got, ref, f"{code.n} T={T}")
+    st = got[1]
+    assert (st == QLDPC_OSD_SOLVED).sum() >= n // 3
+    ok = st == QLDPC_OSD_SOLVED
+    assert (((got[0][ok].astype(np.int64) @ P.H.T.astype(np.int64)) % 2) == sig[ok]).all()
+
+
+def test_edge_cases_cap_empty_ranking_zero_syndrome_and_skip():
+    P = phenomenological_dem(BB144, 12, 0.02)
+    F, sig = _shots(P, 64, 5)
+    sig[:4] = 0                                         # zero syndromes
+    # tiny cap: most shots have too many candidates
+    prm = OSDParams(25, 8.0, 3)
+    _assert_same(_gpu_osd(P, sig, prm), _oracle_osd(P, sig, prm), "cap")
+    # threshold below every marginal: R empty; only zero syndromes are solvable
+    prm = OSDParams(25, -1e6, 500)
+    got = _gpu_osd(P, sig, prm)
+    _assert_same(got, _oracle_osd(P, sig, prm), "empty")
+    assert (got[1][:4] == QLDPC_OSD_SOLVED).all() and not got[0][:4].any()
+    assert (got[1][4:] == -2).all()
+    # no BP iteration: the ranking is by priors alone
+    prm = OSDParams(0, 8.0, 1024)
+    _assert_same(_gpu_osd(P, sig, prm), _oracle_osd(P, sig, prm), "bp0")
+    # skipped shots keep their corrections and report status 0
+    prm = OSDParams(25, 8.0, 500)
+    skip = np.zeros(64, bool)
+    skip[::3] = True
+    init = np.zeros((64, P.N), np.uint8)
+    init[:, 7] = 1
+    cor, st, nc = _gpu_osd(P, sig, prm, skip=skip, init=init)
+    assert (st[skip] == QLDPC_OSD_SKIPPED).all() and (nc[skip] == 0).all()
+    assert (cor[skip] == init[skip]).all()
+    ref = _oracle_osd(P, sig[~skip], prm)
+    _assert_same((cor[~skip], st[~skip], nc[~skip]), ref, "skip")
+    failed = ~skip & (st != QLDPC_OSD_SOLVED)
+    assert (cor[failed] == init[failed]).all()
+
+
+def test_first_leg_then_osd_pipeline_matches_oracle():
+    P = phenomenological_dem(BB144, 12, 0.02)
+    F, sig = _shots(P, 8000, 21)
+    g0 = gamma_table(P.N, 0, 0.125, -0.24, 0.66, 3)
+    first = RelayDecoder(P.row_ptr, P.col_idx, P.p, g0,
+                         RelayConfig(legs_after_first=0, stop_after_solutions=1))
+    prm = OSDParams(25, 8.0, 500)
+    osd = FilteredOSD(P.row_ptr, P.col_idx, P.p, prm.bp_iters, prm.llr_confident,
+                      prm.max_candidates)
+    syn = torch.from_numpy(pack_bits(sig).view(np.int64)).cuda()
+    cor, st, nc, conv = first_leg_then_osd(first, osd, syn)
+    torch.cuda.synchronize()
+    cor = unpack_bits(cor.cpu().numpy().view(np.uint64), P.N)
+    st, nc, conv = st.cpu().numpy(), nc.cpu().numpy(), conv.cpu().numpy()
+    first.close()
+    osd.close()
+    todo = np.nonzero(conv == 0)[0]
+    assert todo.size >= 20
+    Fo, sto, nco = oracle_pipeline(P.H, P.row_ptr, P.col_idx, P.p, g0[0], sig[todo], prm)
+    assert (st[todo] == sto).all() and (nc[todo] == nco).all()
+    assert (cor[todo] == Fo).all()
+    assert (st[conv == 1] == QLDPC_OSD_SKIPPED).all()
