@@ -203,6 +203,15 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
+def kernel_source_sha1() -> str:
+    """sha1 (12 hex digits) of the fused decode kernel's sources, in include order."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("relay_device.cuh", "relay_fused.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2511_21660_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
 def traffic_per_launch(args):
     """DRAM bytes (read + write) of one decode launch, from the committed ncu summary.
 
@@ -210,14 +219,13 @@ def traffic_per_launch(args):
     dram__bytes_write.sum for a 20,000-shot launch of the same kernel; DRAM traffic
     (syndromes in, corrections out, graph and gamma rows) grows with the shot count,
     so it is scaled to the benchmark's shots.  None when the summary is absent or
-    was taken on a different kernel source (its sha1 is recorded in the summary).
+    was taken on a different kernel source (the sha1 of relay_device.cuh followed by
+    relay_fused.cu is recorded in the summary).
     """
-    import hashlib
     path = os.path.join(ROOT, "profiles", "fused_decode_gross_T12.md")
-    src = os.path.join(ROOT, "paper_2511_21660_gb300", "csrc", "relay_fused.cu")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    sha = kernel_source_sha1()
     rd = wr = shots = None
     same_source = False
     for line in open(path):
@@ -280,6 +288,85 @@ def run_decode_only(args):
                       "blocks_per_sm": dec.info.blocks_per_sm, "grid": dec.info.grid_blocks,
                       "smem_bytes": dec.info.smem_bytes}), flush=True)
     dec.close()
+
+
+def osd_variant(args, dev, stream, flush):
+    """First Relay leg + filtered-OSD (paper Sec. 5, Sec. 7.1) against full Relay on the
+    gross 12-round model at p = 0.02, where the first leg leaves about 1% of the shots
+    unconverged: the post-processor's time on those shots, its outcomes, and both
+    decoders' logical error rates on the same 10^5 shots."""
+    import torch
+
+    from paper_2511_21660_gb300 import (QLDPC_OSD_NO_SOLUTION, QLDPC_OSD_SOLVED,
+                                        QLDPC_OSD_TOO_MANY, FilteredOSD, RelayConfig,
+                                        RelayDecoder)
+    from workloads.torch_sampling import pack_bits_t, sample_faults_t, syndromes_t
+    p, n, conf, rmax = 0.02, SHOTS, 8.0, 500
+    P = phenomenological_dem(BB144, 12, p)
+    F = sample_faults_t(P.p, 2, n, device=dev)
+    syn = pack_bits_t(syndromes_t(P.H, F))
+    gam = gamma_table(P.N, 300, 0.125, -0.24, 0.66, 2)
+    first = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam[:1],
+                         RelayConfig(legs_after_first=0, stop_after_solutions=1), device=dev.index)
+    relay = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam,
+                         RelayConfig(stop_after_solutions=S_SOLUTIONS), device=dev.index)
+    osd = FilteredOSD(P.row_ptr, P.col_idx, P.p, 25, conf, rmax, device=dev.index)
+    fo = first.outputs(n)
+    ms_first = sum(timed_decode(first, syn, fo, 3, 3, stream, flush)) / 3
+    ro = relay.outputs(n)
+    ms_relay = sum(timed_decode(relay, syn, ro, 3, 2, stream, flush)) / 3
+    skip = fo[2]
+    cor = torch.empty_like(fo[0])
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    ncand = torch.empty(n, dtype=torch.int32, device=dev)
+    times = []
+    for k in range(6):
+        cor.copy_(fo[0])
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            osd.decode(syn, cor, skip=skip, status=status, n_candidates=ncand, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            times.append(e0.elapsed_time(e1))
+    ms_osd = sum(times) / len(times)
+    A = torch.from_numpy(P.A.astype(np.float32)).to(dev)
+    shifts = torch.arange(64, dtype=torch.int64, device=dev)
+
+    def logical(c):
+        bits = ((c[:, :, None] >> shifts) & 1).reshape(n, -1)[:, :P.N].to(torch.uint8)
+        return ((F ^ bits).to(torch.float32) @ A.T).to(torch.int64).remainder(2).any(1)
+    fail_first = (logical(cor) | ((skip == 0) & (status != QLDPC_OSD_SOLVED))).sum().item()
+    fail_relay = (logical(ro[0]) | (ro[2] == 0)).sum().item()
+    todo = int((skip == 0).sum().item())
+    st = status[skip == 0]
+    out = {"workload": "gross [[144,12,12]] phenomenological T=12, p=0.02, 10^5 shots",
+           "osd": f"25 plain BP iterations, Lambda_confident={conf}, |R|_max={rmax}",
+           "first_leg_ms": ms_first, "first_leg_failures": todo,
+           "osd_ms": ms_osd, "osd_shots_per_s": todo / (ms_osd / 1e3) if todo else None,
+           "osd_status": {"solved": int((st == QLDPC_OSD_SOLVED).sum().item()),
+                          "too_many": int((st == QLDPC_OSD_TOO_MANY).sum().item()),
+                          "no_solution": int((st == QLDPC_OSD_NO_SOLUTION).sum().item())},
+           "mean_candidates": float(ncand[skip == 0].float().mean().item()) if todo else 0.0,
+           "ler_first_leg_plus_osd": fail_first / n, "ler_relay_S5": fail_relay / n,
+           "relay_ms": ms_relay}
+    if args.cpu_baseline and todo:
+        from oracle.osd import OSDParams, bp_llrs, filtered_osd
+        idx = torch.nonzero(skip == 0).flatten()[:40].cpu().numpy()
+        sig = syndromes_t(P.H, F[torch.from_numpy(idx).to(dev)]).cpu().numpy()
+        t0 = time.perf_counter()
+        L = bp_llrs(P.row_ptr, P.col_idx, P.p, sig, 25)
+        for b in range(sig.shape[0]):
+            filtered_osd(P.H, sig[b], L[b], OSDParams(25, conf, rmax))
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": sig.shape[0] / dt, "unit": "post-processed shots/s",
+                               "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"the first {sig.shape[0]} unconverged shots"}
+    for d in (first, relay, osd):
+        d.close()
+    return out
 
 
 def run_ours(args):
@@ -407,6 +494,7 @@ def run_ours(args):
            "d2h_bytes_per_step": int(SHOTS * (cw * 8 + 4 + 1 + 4))}
     assert np.array_equal(h_cor.numpy(), out[0].cpu().numpy()), "host path differs"
 
+    variants["first_leg_then_filtered_osd"] = osd_variant(args, dev, stream, flush)
     cpu = cpu_oracle_rate(P, sig, gam) if args.cpu_baseline else None
     clocks = clk.summary()
     line = {
