@@ -249,7 +249,7 @@ void qldpc_soft_destroy(qldpc_soft *s);
  *      columns of H_R (free columns 0), found by the streaming ("lifted") Gauss-Jordan
  *      elimination of Sec. 4; no solution fails;
  *   4. F_j = x_r for j = R_r.
- * The paper fixes bp_iters = 25 and |R|_max = 500 (Sec. 7.1, App. on the OSD design);
+ * The paper fixes bp_iters = 25 and |R|_max = 500 (Sec. 7.1, App. A.1);
  * it gives no value for Lambda_confident. */
 typedef struct qldpc_osd qldpc_osd;
 
