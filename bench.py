@@ -279,12 +279,13 @@ def run_decode_only(args):
     out = dec.outputs(args.shots)
     times = timed_decode(dec, syn, out, args.steps, args.warmup, stream, flush)
     iters = int(out[3].sum().item())
+    legs = int(out[1].sum().item())
     ms = sum(times) / len(times)
     print(json.dumps({"mode": "decode-only", "kernel": args.kernel, "msg": args.msg,
                       "S": args.solutions,
                       "shots": args.shots, "ms_per_step": ms,
                       "syndromes_per_s": args.shots / (ms / 1e3),
-                      "iterations": iters, "block_threads": dec.info.block_threads,
+                      "iterations": iters, "legs": legs, "block_threads": dec.info.block_threads,
                       "blocks_per_sm": dec.info.blocks_per_sm, "grid": dec.info.grid_blocks,
                       "smem_bytes": dec.info.smem_bytes}), flush=True)
     dec.close()

@@ -302,17 +302,18 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *m
                                            uint32_t *par, float (&Lam)[VPT],
                                            const float (&bb)[VPT], const float (&gg)[VPT],
                                            float C) {
+    static_assert(VPT <= 32, "one decision bit per fault of the thread");
     const int lane = threadIdx.x & 31;
+    uint32_t dmask = 0u;  // bit r: this thread's fault r is decided (F_j = 1)
 #pragma unroll
     for (int r = 0; r < VPT; ++r) {
         const int j = threadIdx.x + r * NT;
         const bool valid = j < g.N;
         float L = 0.0f;
-        int deg = 0;
         if (valid) {
             const float lam = __fadd_rn(bb[r], __fmul_rn(gg[r], Lam[r]));
             int sl[DV];
-            deg = load_slots<DV>(g, j, sl);
+            const int deg = load_slots<DV>(g, j, sl);
             L = fault_update<MT, DV>(msg, sl, deg, lam, C);
             Lam[r] = L;
         }
@@ -320,12 +321,19 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *m
         const uint32_t bal = __ballot_sync(FULL, dec);
         const int jb = threadIdx.x - lane + r * NT;
         if (lane == 0 && jb < g.N) fw[jb >> 5] = bal;
-        if (bal != 0u && dec) {  // decided faults are few: flip their checks' parity
-            const int *ck = g.var_chk + (size_t)j * DV;
-            for (int k = 0; k < deg; ++k) {
-                const int c = __ldg(ck + k);
-                atomicXor(par + (c >> 5), 1u << (c & 31));
-            }
+        dmask |= (dec ? 1u : 0u) << r;
+    }
+    // Decided faults are few: flip their checks' parity after the loop, so that the
+    // per-fault body carries no divergent branch and no live edge state.
+    while (dmask) {
+        const int r = __ffs(dmask) - 1;
+        dmask &= dmask - 1u;
+        const int j = threadIdx.x + r * NT;
+        const int deg = (int)((uint32_t)__ldg(g.var_slot + (size_t)j * DV) >> 24);
+        const int *ck = g.var_chk + (size_t)j * DV;
+        for (int k = 0; k < deg; ++k) {
+            const int c = __ldg(ck + k);
+            atomicXor(par + (c >> 5), 1u << (c & 31));
         }
     }
 }
