@@ -282,6 +282,57 @@ int qldpc_osd_decode_batch(qldpc_osd *o, const uint64_t *syndromes, int64_t B,
 /* Wait for the handle's work, then free it.  NULL is ignored. */
 void qldpc_osd_destroy(qldpc_osd *o);
 
+/* ---- Cluster decoder (paper Sec. 2.5 "Cluster decoding" / "BP-UF decoding", Sec. 6,
+ * pre-decoder set-up of Sec. 7.1) ----
+ *
+ * For each shot not marked in `skip` (typically those the first Relay leg leaves
+ * unconverged):
+ *   1. bp_iters iterations of plain min-sum BP from the priors give Lambda;
+ *   2. faults with Lambda_j <= llr_accept form a partial correction F_pre, faults with
+ *      llr_accept < Lambda_j <= llr_erase the erasure set; sigma <- sigma + H F_pre;
+ *   3. one cluster per syndrome check and per erased fault, taken in decreasing node
+ *      index (checks before faults); clusters are vertex sets of the Tanner graph;
+ *   4. while a cluster is invalid (its syndrome is not in the image of H restricted to
+ *      its checks and interior faults), the first invalid one is grown by all neighbours
+ *      of its vertices, merged with every cluster it meets, re-tested, and queued last
+ *      if still invalid;
+ *   5. the correction is F_pre + each cluster's solution on its interior faults (free
+ *      columns 0, columns in increasing fault index).
+ * The paper gives N_clus = 50 / 100 and solver sizes up to 144 x 288 / 576 x 1152
+ * (App. A.2) and no values for the cutoffs. */
+typedef struct qldpc_cluster qldpc_cluster;
+
+typedef struct {
+    int32_t bp_iters;           /* >= 0 plain BP iterations (paper 25)                       */
+    float llr_accept;           /* Lambda_j <= llr_accept: partial correction (finite)      */
+    float llr_erase;            /* llr_accept < Lambda_j <= llr_erase: erasure (finite)     */
+    int32_t max_clusters;       /* 1..4096 initial clusters; more fails                     */
+    int32_t max_cluster_faults; /* 1..512 interior faults of one cluster; more fails        */
+} qldpc_cluster_params;
+
+#define QLDPC_CLUSTER_SKIPPED 0       /* skip[b] != 0: nothing written                       */
+#define QLDPC_CLUSTER_DECODED 1       /* every cluster valid; corrections[b] written         */
+#define QLDPC_CLUSTER_TOO_LARGE (-1)  /* a cluster exceeded max_cluster_faults               */
+#define QLDPC_CLUSTER_TOO_MANY (-2)   /* more than max_clusters initial clusters             */
+#define QLDPC_CLUSTER_STALLED (-3)    /* the update loop exceeded M + N steps (not expected)  */
+
+/* Copy H (CSR as in qldpc_create, M + N <= 32767, check degree <= 32, fault degree <= 8)
+ * and the priors to `device`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
+int qldpc_cluster_create(qldpc_cluster **out, int32_t M, int32_t N, const int32_t *row_ptr,
+                         const int32_t *col_idx, const double *priors,
+                         const qldpc_cluster_params *params, int device);
+
+/* Decode B shots (device pointers): syndromes [B][ceil(M/64)] u64; skip [B] u8 or NULL;
+ * corrections [B][ceil(N/64)] u64, written only for decoded shots; status [B] int32
+ * (QLDPC_CLUSTER_*); steps [B] int32 growth steps or NULL.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, CUDA. */
+int qldpc_cluster_decode_batch(qldpc_cluster *c, const uint64_t *syndromes, int64_t B,
+                               const uint8_t *skip, uint64_t *corrections, int32_t *status,
+                               int32_t *steps, void *stream);
+
+/* Wait for the handle's work, then free it.  NULL is ignored. */
+void qldpc_cluster_destroy(qldpc_cluster *c);
+
 /* Fill *info.  Errors: INVALID_ARG. */
 int qldpc_get_info(const qldpc_decoder *d, qldpc_info *info);
 

@@ -26,7 +26,8 @@ FUSED_FAMILIES = [(0, 8, 4), (0, 16, 8), (0, 32, 8), (1, 8, 4), (1, 16, 8), (1, 
 
 def _units():
     units = [("qldpc_api", "qldpc_api.cu", []), ("relay_baseline", "relay_baseline.cu", []),
-             ("soft_dmem", "soft_dmem.cu", []), ("filtered_osd", "filtered_osd.cu", [])]
+             ("soft_dmem", "soft_dmem.cu", []), ("filtered_osd", "filtered_osd.cu", []),
+             ("cluster_decode", "cluster_decode.cu", [])]
     for f16, dc, dv in FUSED_FAMILIES:
         units.append((f"relay_fused_{'f16' if f16 else 'f32'}_{dc}_{dv}", "relay_fused.cu",
                       [f"-DQL_MSG_F16={f16}", f"-DQL_DC={dc}", f"-DQL_DV={dv}"]))

@@ -1,0 +1,410 @@
+// Cluster decoder after plain BP (paper Sec. 2.5, "Cluster decoding" and "BP-UF
+// decoding"; its FPGA form in Sec. 6; pre-decoder set-up of Sec. 7.1), one thread block
+// per shot at a time:
+//
+//   1. plain min-sum BP for bp_iters iterations from the priors (relay_device.cuh);
+//   2. input (Sec. 6.2): faults with Lambda_j <= llr_accept form the partial correction
+//      F_pre, faults with llr_accept < Lambda_j <= llr_erase the erasure set;
+//      sigma <- sigma + H F_pre by parity atomics;
+//   3. initialisation (Sec. 6.3): one cluster per syndrome check and per erased fault,
+//      numbered in seed-extraction order (right-most bit of the initialisation bitmap
+//      first: decreasing check index, then decreasing fault index); the single-check
+//      clusters are the invalid list, the erased-fault clusters start valid (no check,
+//      no interior fault);
+//   4. update loop (Sec. 6.4-6.7): the first invalid cluster c is grown by every
+//      neighbour of its vertices, every cluster the grown set meets is merged into c
+//      (and leaves the invalid list), the interior faults of c are found, and c is
+//      tested by the streaming GF(2) solver of one warp (gf2_warp.cuh) on its checks
+//      (rows, increasing index) and interior faults (columns, increasing index); an
+//      invalid c goes to the end of the list;
+//   5. output (Sec. 6.8): each surviving cluster's solution with free columns 0; the
+//      correction is F_pre + the union of those.
+//
+// Clusters are kept as one 16-bit label per vertex (checks 0..M-1, faults M..M+N-1)
+// instead of one bitmap per cluster: growth, merge detection and relabelling are then
+// three block-wide passes over the vertices, whatever the number of clusters.
+#include "gf2_warp.cuh"
+#include "relay_device.cuh"
+
+namespace qldpc {
+namespace {
+
+// Exclusive prefix of the popcounts of words[0..nw) into pre[], by one warp; returns
+// the total on every lane.
+__device__ __forceinline__ int warp_word_prefix(const uint32_t *words, uint32_t *pre, int nw) {
+    const int lane = threadIdx.x & 31;
+    const int ch = (nw + 31) / 32;
+    const int w0 = lane * ch, w1 = min(nw, w0 + ch);
+    int local = 0;
+    for (int w = w0; w < w1; ++w) local += __popc(words[w]);
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int run = incl - local;
+    for (int w = w0; w < w1; ++w) {
+        pre[w] = (uint32_t)run;
+        run += __popc(words[w]);
+    }
+    return __shfl_sync(FULL, incl, 31);
+}
+
+// Set bits of words at or below position b of its word.
+__device__ __forceinline__ uint32_t mask_upto(int b) {
+    return b == 31 ? 0xffffffffu : ((2u << b) - 1u);
+}
+
+__device__ __forceinline__ void set_bit(uint32_t *bm, int v) {
+    atomicOr(bm + (v >> 5), 1u << (v & 31));
+}
+
+__device__ __forceinline__ bool get_bit(const uint32_t *bm, int v) {
+    return (bm[v >> 5] >> (v & 31)) & 1u;
+}
+
+template <int DV>
+__device__ __forceinline__ int fault_degree(const FusedGraph &g, int j) {
+    return (int)((uint32_t)__ldg(g.var_slot + (size_t)j * DV) >> 24);
+}
+
+// Fault j belongs to cluster `lab` and so does each of its checks.
+template <int DV>
+__device__ __forceinline__ bool interior_of(const FusedGraph &g, const int16_t *label, int j,
+                                            int lab) {
+    if (label[g.M + j] != lab) return false;
+    const int deg = fault_degree<DV>(g, j);
+    for (int k = 0; k < deg; ++k)
+        if (label[__ldg(g.var_chk + (size_t)j * DV + k)] != lab) return false;
+    return true;
+}
+
+// Streams the rows of cluster `lab` (its checks, increasing index) into the warp's
+// solver; columns are the cluster's interior faults (bitmap intr, word prefix wpre).
+// Returns false when the system has no solution.  Called by warp 0.
+template <int DC>
+__device__ __forceinline__ bool stream_cluster_rows(const FusedGraph &g, const ClusterArgs &a,
+                                                    const int16_t *label, int lab,
+                                                    const uint32_t *intr, const uint32_t *wpre,
+                                                    const uint32_t *sp, uint32_t &lockw,
+                                                    uint32_t &specw, uint32_t *up, int ncols) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < g.M; base += 32) {
+        const int i = base + lane;
+        uint32_t bal = __ballot_sync(FULL, i < g.M && label[i] == lab);
+        while (bal) {
+            const int ci = base + __ffs(bal) - 1;
+            bal &= bal - 1u;
+            int pr = -1;
+            if (lane < DC) {
+                const int jv = __ldg(a.chk_var + (size_t)ci * DC + lane);
+                if (jv >= 0 && get_bit(intr, jv))
+                    pr = (int)wpre[jv >> 5] +
+                         __popc(intr[jv >> 5] & ((1u << (jv & 31)) - 1u));
+            }
+            const uint32_t row = gf2::row_from_positions(pr, DC);
+            const uint32_t spec = (sp[ci >> 5] >> (ci & 31)) & 1u;
+            if (!gf2::insert_row(row, spec, lockw, specw, up, a.W, ncols)) return false;
+        }
+    }
+    return true;
+}
+
+template <int NT, int VPT, int DC, int DV>
+__global__ void __launch_bounds__(NT, 1) cluster_decode(FusedGraph g, DevParams p, ClusterArgs a,
+                                                        const uint64_t *__restrict__ syn,
+                                                        const uint8_t *__restrict__ skip, int B,
+                                                        ClusterOut out, unsigned int *counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *msg = smem_raw;
+    const ClusterLayout L = cluster_layout(g, a);
+    int16_t *label = reinterpret_cast<int16_t *>(smem_raw + L.label);
+    uint32_t *grown = reinterpret_cast<uint32_t *>(smem_raw + L.grown);
+    uint32_t *intr = reinterpret_cast<uint32_t *>(smem_raw + L.intr);
+    uint32_t *wpre = reinterpret_cast<uint32_t *>(smem_raw + L.wpre);
+    uint32_t *fpre = reinterpret_cast<uint32_t *>(smem_raw + L.fpre);
+    uint32_t *fera = reinterpret_cast<uint32_t *>(smem_raw + L.fera);
+    uint32_t *fout = reinterpret_cast<uint32_t *>(smem_raw + L.fout);
+    uint32_t *sp = reinterpret_cast<uint32_t *>(smem_raw + L.sp);
+    uint32_t *spre = reinterpret_cast<uint32_t *>(smem_raw + L.spre);
+    uint8_t *mflag = smem_raw + L.flags;
+    int16_t *queue = reinterpret_cast<int16_t *>(smem_raw + L.queue);
+    uint32_t *up = reinterpret_cast<uint32_t *>(smem_raw + L.up);
+    uint32_t *fw = reinterpret_cast<uint32_t *>(smem_raw + cluster_union_bytes(g, a));
+    uint32_t *fb = fw + g.f_words;
+    uint32_t *sg = fb + g.f_words;
+    uint32_t *par = sg + 2 * g.syn_words;
+    float *ws = reinterpret_cast<float *>(par + 2 * g.m_words);
+    __shared__ int s_shot, s_ns, s_ne, s_status, s_c, s_head, s_count, s_steps, s_nint, s_valid;
+    __shared__ uint32_t s_x[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int V = g.M + g.N, VW = (V + 31) / 32, NW = (g.N + 31) / 32;
+    const int NWp = 2 * g.cor_words;  // fault bitmaps padded to whole 64-bit words
+    const int MW = g.m_words, KC = a.max_clusters;
+
+    float Lam[VPT], bb[VPT], gg[VPT];
+#pragma unroll
+    for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
+
+    for (;;) {
+        __syncthreads();  // the previous shot is done with shared memory
+        if (tid == 0) s_shot = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int shot = s_shot;
+        if (shot >= B) break;
+        if (skip && skip[shot]) {
+            if (tid == 0) {
+                out.status[shot] = 0;
+                if (out.steps) out.steps[shot] = 0;
+            }
+            continue;
+        }
+
+        // 1. plain BP
+        if (tid == 0) {
+            s_status = 1;
+            s_steps = 0;
+        }
+        plain_bp<NT, VPT, DC, DV>(g, p, a.bp_iters, syn + (size_t)shot * g.syn_words, msg, fw,
+                                  sg, par, ws, Lam, bb, gg);
+
+        // 2. partial correction and erasures; sigma + H F_pre
+        uint32_t pmask = 0u;
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) {
+            const int j = tid + r * NT;
+            const bool valid = j < g.N;
+            const float x = Lam[r];
+            const bool pre = valid && x <= a.llr_accept;
+            const bool era = valid && x > a.llr_accept && x <= a.llr_erase;
+            const uint32_t bp_ = __ballot_sync(FULL, pre), be = __ballot_sync(FULL, era);
+            const int jb = tid - lane + r * NT;
+            if (lane == 0 && jb < g.N) {
+                fpre[jb >> 5] = bp_;
+                fera[jb >> 5] = be;
+            }
+            pmask |= (pre ? 1u : 0u) << r;
+        }
+        if (tid == 0)
+            for (int q = NW; q < NWp; ++q) fpre[q] = fera[q] = 0u;
+        for (int q = tid; q < MW; q += NT) sp[q] = sg[q];
+        __syncthreads();
+        while (pmask) {
+            const int r = __ffs(pmask) - 1;
+            pmask &= pmask - 1u;
+            const int j = tid + r * NT;
+            const int deg = fault_degree<DV>(g, j);
+            for (int k = 0; k < deg; ++k) {
+                const int c = __ldg(g.var_chk + (size_t)j * DV + k);
+                atomicXor(sp + (c >> 5), 1u << (c & 31));
+            }
+        }
+        __syncthreads();
+
+        // 3. seeds, numbered right-most first: checks, then erased faults
+        if (warp == 0) {
+            const int ns = warp_word_prefix(sp, spre, MW);
+            if (lane == 0) s_ns = ns;
+        } else if (warp == 1) {
+            const int ne = warp_word_prefix(fera, wpre, NWp);
+            if (lane == 0) s_ne = ne;
+        }
+        __syncthreads();
+        const int ns = s_ns, ne = s_ne;
+        if (ns + ne > KC) {
+            if (tid == 0) {
+                out.status[shot] = -2;
+                if (out.steps) out.steps[shot] = 0;
+            }
+            continue;
+        }
+        for (int v = tid; v < V; v += NT) {
+            int16_t lab = -1;
+            if (v < g.M) {
+                if (get_bit(sp, v))
+                    lab = (int16_t)(ns - (int)spre[v >> 5] -
+                                    __popc(sp[v >> 5] & mask_upto(v & 31)));
+            } else {
+                const int j = v - g.M;
+                if (get_bit(fera, j))
+                    lab = (int16_t)(ns + ne - (int)wpre[j >> 5] -
+                                    __popc(fera[j >> 5] & mask_upto(j & 31)));
+            }
+            label[v] = lab;
+        }
+        for (int q = tid; q < KC; q += NT) {
+            mflag[q] = 0;
+            queue[q] = (int16_t)q;  // the invalid list starts as the check seeds 0..ns-1
+        }
+        if (tid == 0) {
+            s_head = 0;
+            s_count = ns;
+        }
+        __syncthreads();
+
+        // 4. update loop: every step adds a vertex to a cluster, so at most V steps
+        for (;;) {
+            if (tid == 0) {
+                if (s_count == 0 || s_steps >= V) {
+                    s_c = -1;
+                    if (s_count != 0) s_status = -3;
+                } else {
+                    s_c = queue[s_head];
+                    s_head = s_head + 1 == KC ? 0 : s_head + 1;
+                    --s_count;
+                    ++s_steps;
+                }
+            }
+            for (int q = tid; q < VW; q += NT) grown[q] = 0u;
+            __syncthreads();
+            const int c = s_c;
+            if (c < 0) break;
+            // grow: every vertex of c and its neighbours
+            for (int v = tid; v < V; v += NT) {
+                if (label[v] != c) continue;
+                set_bit(grown, v);
+                if (v < g.M) {
+                    for (int k = 0; k < DC; ++k) {
+                        const int jv = __ldg(a.chk_var + (size_t)v * DC + k);
+                        if (jv < 0) break;
+                        set_bit(grown, g.M + jv);
+                    }
+                } else {
+                    const int j = v - g.M, deg = fault_degree<DV>(g, j);
+                    for (int k = 0; k < deg; ++k)
+                        set_bit(grown, __ldg(g.var_chk + (size_t)j * DV + k));
+                }
+            }
+            __syncthreads();
+            // merge: the clusters the grown set meets
+            for (int v = tid; v < V; v += NT) {
+                const int lab = label[v];
+                if (lab >= 0 && lab != c && get_bit(grown, v)) mflag[lab] = 1;
+            }
+            __syncthreads();
+            for (int v = tid; v < V; v += NT) {
+                const int lab = label[v];
+                if (get_bit(grown, v) || (lab >= 0 && mflag[lab])) label[v] = (int16_t)c;
+            }
+            if (tid == 0) {  // merged clusters leave the invalid list
+                int k = 0;
+                for (int q = 0; q < s_count; ++q) {
+                    const int at = (s_head + q) % KC;
+                    const int id = queue[at];
+                    if (!mflag[id]) queue[(s_head + k++) % KC] = (int16_t)id;
+                }
+                s_count = k;
+            }
+            __syncthreads();
+            for (int q = tid; q < ns + ne; q += NT) mflag[q] = 0;
+            for (int q = tid; q < NWp; q += NT) intr[q] = 0u;
+            __syncthreads();
+            // interior faults of c
+            for (int j = tid; j < g.N; j += NT)
+                if (interior_of<DV>(g, label, j, c)) set_bit(intr, j);
+            __syncthreads();
+            if (warp == 0) {
+                const int n = warp_word_prefix(intr, wpre, NWp);
+                if (lane == 0) s_nint = n;
+            }
+            __syncthreads();
+            const int n = s_nint;
+            if (n > a.max_cols) {
+                if (tid == 0) s_status = -1;
+                break;
+            }
+            // validity of c by warp 0
+            if (warp == 0) {
+                uint32_t lockw = 0u, specw = 0u;
+                const bool ok = stream_cluster_rows<DC>(g, a, label, c, intr, wpre, sp, lockw,
+                                                        specw, up, n);
+                if (lane == 0) s_valid = ok;
+            }
+            __syncthreads();
+            if (tid == 0 && !s_valid) {
+                queue[(s_head + s_count) % KC] = (int16_t)c;
+                ++s_count;
+            }
+        }
+        __syncthreads();
+        if (s_status != 1) {
+            if (tid == 0) {
+                out.status[shot] = s_status;
+                if (out.steps) out.steps[shot] = s_steps;
+            }
+            continue;
+        }
+
+        // 5. solutions of the clusters that own an interior fault
+        for (int q = tid; q < NWp; q += NT) fout[q] = 0u;
+        for (int j = tid; j < g.N; j += NT) {
+            const int lab = label[g.M + j];
+            if (lab >= 0 && interior_of<DV>(g, label, j, lab)) mflag[lab] = 1;
+        }
+        __syncthreads();
+        for (int id = 0; id < ns + ne; ++id) {
+            if (!mflag[id]) continue;  // uniform: every thread reads the same flag
+            for (int q = tid; q < NWp; q += NT) intr[q] = 0u;
+            __syncthreads();
+            for (int j = tid; j < g.N; j += NT)
+                if (interior_of<DV>(g, label, j, id)) set_bit(intr, j);
+            __syncthreads();
+            if (warp == 0) {
+                const int n = warp_word_prefix(intr, wpre, NWp);
+                uint32_t lockw = 0u, specw = 0u;
+                stream_cluster_rows<DC>(g, a, label, id, intr, wpre, sp, lockw, specw, up, n);
+                s_x[lane] = gf2::back_substitute(lockw, specw, up, a.W, n);
+            }
+            __syncthreads();
+            for (int j = tid; j < g.N; j += NT) {
+                if (!get_bit(intr, j)) continue;
+                const int pc = (int)wpre[j >> 5] + __popc(intr[j >> 5] & ((1u << (j & 31)) - 1u));
+                if ((s_x[pc >> 5] >> (pc & 31)) & 1u) set_bit(fout, j);
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < g.cor_words; q += NT)
+            out.corr[(size_t)shot * g.cor_words + q] =
+                (uint64_t)(fout[2 * q] ^ fpre[2 * q]) |
+                ((uint64_t)(fout[2 * q + 1] ^ fpre[2 * q + 1]) << 32);
+        if (tid == 0) {
+            out.status[shot] = 1;
+            if (out.steps) out.steps[shot] = s_steps;
+        }
+    }
+}
+
+template <int NT, int VPT, int DC, int DV>
+cudaError_t launch_cluster(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
+                           const DevParams &p, const ClusterArgs &a, const uint64_t *syn,
+                           const uint8_t *skip, int B, ClusterOut out, unsigned int *counter) {
+    cluster_decode<NT, VPT, DC, DV><<<grid, NT, smem, st>>>(g, p, a, syn, skip, B, out, counter);
+    return cudaGetLastError();
+}
+
+template <int NT, int VPT, int DC, int DV>
+ClusterKernel cluster_entry() {
+    ClusterKernel k;
+    k.threads = NT;
+    k.vpt = VPT;
+    k.dc = DC;
+    k.dv = DV;
+    k.fn = (const void *)cluster_decode<NT, VPT, DC, DV>;
+    k.launch = &launch_cluster<NT, VPT, DC, DV>;
+    return k;
+}
+
+}  // namespace
+
+void cluster_table(const ClusterKernel **out, int *n) {
+    // per (DC, DV) family of the fused layout: the first entry with threads * vpt >= N
+    static const ClusterKernel table[] = {
+        cluster_entry<512, 8, 8, 4>(),  cluster_entry<512, 16, 8, 4>(),
+        cluster_entry<512, 8, 16, 8>(), cluster_entry<512, 16, 16, 8>(),
+        cluster_entry<512, 8, 32, 8>(), cluster_entry<512, 16, 32, 8>(),
+    };
+    *out = table;
+    *n = (int)(sizeof(table) / sizeof(table[0]));
+}
+
+}  // namespace qldpc

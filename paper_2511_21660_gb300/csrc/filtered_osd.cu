@@ -11,15 +11,16 @@
 //      checks touched by R are marked; an untouched check with sigma_i = 1 makes the
 //      system unsolvable; only touched rows are streamed;
 //   4. solver (Sec. 4, Algorithm "Lifted Gauss-Jordan over F_2", as the paper's
-//      systolic solver applies it): one warp streams the touched rows in check order;
-//      a row is reduced by locked pivot rows until its leftmost 1 (in ranking order)
-//      is an unlocked column, where it is stored with its syndrome bit; a row reduced
-//      to zero with syndrome bit 1 means no solution.  Back substitution over the
-//      locked columns, from the right, gives x with free columns 0;
+//      systolic solver applies it; gf2_warp.cuh): one warp streams the touched rows in
+//      check order; a row is reduced by locked pivot rows until its leftmost 1 (in
+//      ranking order) is an unlocked column, where it is stored with its syndrome bit;
+//      a row reduced to zero with syndrome bit 1 means no solution.  Back substitution
+//      over the locked columns, from the right, gives x with free columns 0;
 //   5. F_j = x_r for j = R_r (Sec. 5, "Algorithm output").
 //
 // A pivot row is a W-word bitset over ranking positions held by lanes 0..W-1 (lane l
 // owns word l), so the reduction of a row by a pivot row is one 32-bit XOR per lane.
+#include "gf2_warp.cuh"
 #include "relay_device.cuh"
 
 namespace qldpc {
@@ -70,7 +71,6 @@ __global__ void __launch_bounds__(NT, 1) osd_decode(FusedGraph g, DevParams p, O
     __shared__ int s_shot, s_cnt, s_bad;
     __shared__ uint32_t s_x[32];
     const int tid = threadIdx.x, lane = tid & 31;
-    const float C = p.clip;
 
     float Lam[VPT], bb[VPT], gg[VPT];
 #pragma unroll
@@ -91,21 +91,12 @@ __global__ void __launch_bounds__(NT, 1) osd_decode(FusedGraph g, DevParams p, O
         }
 
         // 1. plain BP: lambda_j(t) = w_j (gamma row of zeros), Lambda from the priors
-        block_setup<float, NT, DC>(g, msg, fw, ws, C);
-        load_syndrome<NT>(g, syn + (size_t)shot * g.syn_words, sg);
         if (tid == 0) {
             s_cnt = 0;
             s_bad = 0;
         }
-        __syncthreads();
-        leg_init<float, NT, VPT, DV>(g, p, 0, msg, ws, Lam, bb, gg);
-        __syncthreads();
-        for (int t = 0; t < o.bp_iters; ++t) {
-            check_pass<NT, DC>(g, reinterpret_cast<float *>(msg), sg, par, C);
-            __syncthreads();
-            fault_pass<float, NT, VPT, DV>(g, msg, fw, par, Lam, bb, gg, C);
-            __syncthreads();
-        }
+        plain_bp<NT, VPT, DC, DV>(g, p, o.bp_iters, syn + (size_t)shot * g.syn_words, msg, fw,
+                                  sg, par, ws, Lam, bb, gg);
 
         // 2. ranking: candidates Lambda_j < llr_conf, keys (Lambda_j, j)
 #pragma unroll
@@ -173,50 +164,15 @@ __global__ void __launch_bounds__(NT, 1) osd_decode(FusedGraph g, DevParams p, O
                         const int jv = __ldg(o.chk_var + (size_t)c * DC + lane);
                         if (jv >= 0) pr = pos[jv];
                     }
-                    uint32_t row = 0u;
-#pragma unroll
-                    for (int s = 0; s < DC; ++s) {
-                        const int ps = __shfl_sync(FULL, pr, s);
-                        if (ps >= 0 && (ps >> 5) == lane) row |= 1u << (ps & 31);
+                    const uint32_t row = gf2::row_from_positions(pr, DC);
+                    const uint32_t spec = (sg[c >> 5] >> (c & 31)) & 1u;
+                    if (!gf2::insert_row(row, spec, lockw, specw, up, o.W, n)) {
+                        bad = true;
+                        break;
                     }
-                    uint32_t spec = (sg[c >> 5] >> (c & 31)) & 1u;
-                    // each reduction clears the row's leading column, so at most n + 1 steps
-                    for (int step = 0; step <= n; ++step) {
-                        const uint32_t nz = __ballot_sync(FULL, row != 0u);
-                        if (nz == 0u) {
-                            bad = spec != 0u;
-                            break;
-                        }
-                        const int wl = __ffs(nz) - 1;
-                        const int bit = __ffs(__shfl_sync(FULL, row, wl)) - 1;
-                        const int pc = 32 * wl + bit;
-                        const uint32_t lk = __shfl_sync(FULL, lockw, wl);
-                        if ((lk >> bit) & 1u) {
-                            if (lane < o.W) row ^= up[(size_t)pc * o.W + lane];
-                            spec ^= (__shfl_sync(FULL, specw, wl) >> bit) & 1u;
-                        } else {
-                            if (lane < o.W) up[(size_t)pc * o.W + lane] = row;
-                            if (lane == wl) {
-                                lockw |= 1u << bit;
-                                specw |= spec << bit;
-                            }
-                            break;
-                        }
-                    }
-                    if (bad) break;
                 }
             }
-            uint32_t xw = 0u;
-            if (!bad) {
-                for (int pc = n - 1; pc >= 0; --pc) {
-                    const int wl = pc >> 5, bit = pc & 31;
-                    if (!((__shfl_sync(FULL, lockw, wl) >> bit) & 1u)) continue;
-                    const uint32_t t = lane < o.W ? (up[(size_t)pc * o.W + lane] & xw) : 0u;
-                    const uint32_t parity = __popc(__ballot_sync(FULL, __popc(t) & 1u)) & 1u;
-                    const uint32_t xp = ((__shfl_sync(FULL, specw, wl) >> bit) & 1u) ^ parity;
-                    if (xp && lane == wl) xw |= 1u << bit;
-                }
-            }
+            const uint32_t xw = bad ? 0u : gf2::back_substitute(lockw, specw, up, o.W, n);
             s_x[lane] = xw;
             if (lane == 0 && bad) s_bad = 1;
         }

@@ -134,6 +134,71 @@ inline size_t osd_smem_bytes(const FusedGraph &g, const OsdArgs &o) {
            8 * (size_t)g.m_words + 4 * (size_t)g.N + 64;
 }
 
+// Cluster decoder (paper Sec. 2.5 and Sec. 6) after plain BP: partial correction,
+// erasures, union-find growth and merging of per-vertex cluster labels, validity by the
+// streaming GF(2) solver of one warp.  Vertices are checks 0..M-1 then faults M..M+N-1.
+constexpr int kClusterMaxColumns = 512;   // interior faults of one cluster (solver width)
+constexpr int kClusterMaxClusters = 4096; // initial clusters (16-bit labels)
+struct ClusterArgs {
+    const int32_t *chk_var;  // [Mp][DC] fault of the k-th edge of check i, -1 past its degree
+    int bp_iters;
+    float llr_accept;        // Lambda_j <= llr_accept: partial correction
+    float llr_erase;         // llr_accept < Lambda_j <= llr_erase: erasure
+    int max_clusters;        // 1..kClusterMaxClusters
+    int max_cols;            // 1..kClusterMaxColumns
+    int W;                   // ceil(max_cols / 32)
+};
+struct ClusterOut {
+    uint64_t *corr;    // [B][cor_words], written for decoded shots only
+    int32_t *status;   // [B] 0 skipped, 1 decoded, -1 cluster too large, -2 too many clusters
+    int32_t *steps;    // [B] growth steps (may be NULL)
+};
+struct ClusterKernel {
+    int threads, vpt, dc, dv;
+    const void *fn;
+    cudaError_t (*launch)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
+                          const DevParams &p, const ClusterArgs &a, const uint64_t *syn,
+                          const uint8_t *skip, int B, ClusterOut out, unsigned int *counter);
+};
+void cluster_table(const ClusterKernel **out, int *n);
+// The cluster stage reuses the message area: labels [M+N] i16, the grown-vertex bitmap,
+// interior / partial-correction / erasure / correction bitmaps over faults, their word
+// prefix counts, the updated syndrome, per-cluster flags and queue, pivot rows.
+struct ClusterLayout {
+    size_t label, grown, intr, wpre, fpre, fera, fout, sp, spre, flags, queue, up, total;
+};
+__host__ __device__ inline ClusterLayout cluster_layout(const FusedGraph &g, const ClusterArgs &a) {
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    // fault bitmaps padded to whole 64-bit words (the correction's layout)
+    const size_t V = (size_t)g.M + g.N, VW = (V + 31) / 32, NW = 2 * (size_t)g.cor_words;
+    const size_t MW = (size_t)g.m_words;
+    ClusterLayout L;
+    size_t o = 0;
+    L.label = o; o = al(o + 2 * V);
+    L.grown = o; o = al(o + 4 * VW);
+    L.intr = o;  o = al(o + 4 * NW);
+    L.wpre = o;  o = al(o + 4 * NW);
+    L.fpre = o;  o = al(o + 4 * NW);
+    L.fera = o;  o = al(o + 4 * NW);
+    L.fout = o;  o = al(o + 4 * NW);
+    L.sp = o;    o = al(o + 4 * MW);
+    L.spre = o;  o = al(o + 4 * (MW > NW ? MW : NW));
+    L.flags = o; o = al(o + 2 * (size_t)a.max_clusters);   // merge flag, alive flag
+    L.queue = o; o = al(o + 2 * (size_t)a.max_clusters);
+    L.up = o;    o = al(o + 4 * (size_t)a.max_cols * a.W);
+    L.total = o;
+    return L;
+}
+__host__ __device__ inline size_t cluster_union_bytes(const FusedGraph &g, const ClusterArgs &a) {
+    const size_t msg = ((size_t)g.msg_bytes + 15) & ~(size_t)15;
+    const size_t c = cluster_layout(g, a).total;
+    return msg > c ? msg : c;
+}
+inline size_t cluster_smem_bytes(const FusedGraph &g, const ClusterArgs &a) {
+    return cluster_union_bytes(g, a) + 8 * (size_t)g.f_words + 8 * (size_t)g.syn_words +
+           8 * (size_t)g.m_words + 4 * (size_t)g.N + 64;
+}
+
 // Tables of compiled fused kernels, one per (precision, DC, DV) translation unit.
 #define QLDPC_DECLARE_TABLE(P, DC, DV) \
     void fused_table_##P##_##DC##_##DV(const FusedKernel **out, int *n);

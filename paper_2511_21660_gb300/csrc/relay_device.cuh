@@ -404,6 +404,17 @@ __device__ __forceinline__ void smem_layout(const FusedGraph &g, unsigned char *
     ws = reinterpret_cast<float *>(par + 2 * g.m_words);
 }
 
+// Plain min-sum BP (paper Sec. 2.3, "Belief propagation decoding"): DMem-BP with every
+// gamma_j = 0, which the graph's gamma row (all zeros) provides, from the priors, for
+// `iters` iterations without early exit; the marginals end in Lam.  Re-stages the
+// padding slots and priors first (callers reuse the message area between shots).
+// Called by every thread of the block.
+template <int NT, int VPT, int DC, int DV>
+__device__ __forceinline__ void plain_bp(const FusedGraph &g, const DevParams &p, int iters,
+                                         const uint64_t *sy, unsigned char *msg, uint32_t *fw,
+                                         uint32_t *sg, uint32_t *par, float *ws,
+                                         float (&Lam)[VPT], float (&bb)[VPT], float (&gg)[VPT]);
+
 // Is the decision bitmap equal to the kept solution?  Each warp decides on its own.
 __device__ __forceinline__ bool warp_same_solution(const uint32_t *fw, const uint32_t *fb,
                                                    int words) {
@@ -439,6 +450,25 @@ __device__ __forceinline__ void load_syndrome(const FusedGraph &g, const uint64_
         if (hi < 64) v &= (1ull << hi) - 1ull;
         sg[2 * q] = (uint32_t)v;
         sg[2 * q + 1] = (uint32_t)(v >> 32);
+    }
+}
+
+
+template <int NT, int VPT, int DC, int DV>
+__device__ __forceinline__ void plain_bp(const FusedGraph &g, const DevParams &p, int iters,
+                                         const uint64_t *sy, unsigned char *msg, uint32_t *fw,
+                                         uint32_t *sg, uint32_t *par, float *ws,
+                                         float (&Lam)[VPT], float (&bb)[VPT], float (&gg)[VPT]) {
+    block_setup<float, NT, DC>(g, msg, fw, ws, p.clip);
+    load_syndrome<NT>(g, sy, sg);
+    __syncthreads();
+    leg_init<float, NT, VPT, DV>(g, p, 0, msg, ws, Lam, bb, gg);
+    __syncthreads();
+    for (int t = 0; t < iters; ++t) {
+        check_pass<NT, DC>(g, reinterpret_cast<float *>(msg), sg, par, p.clip);
+        __syncthreads();
+        fault_pass<float, NT, VPT, DV>(g, msg, fw, par, Lam, bb, gg, p.clip);
+        __syncthreads();
     }
 }
 

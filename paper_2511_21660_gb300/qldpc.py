@@ -31,7 +31,13 @@ EXPORTED = ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
             "qldpc_destroy", "qldpc_status_string", "qldpc_last_error", "qldpc_soft_create",
             "qldpc_soft_workspace_bytes", "qldpc_soft_forward", "qldpc_soft_backward",
             "qldpc_soft_destroy", "qldpc_osd_create", "qldpc_osd_decode_batch",
-            "qldpc_osd_destroy")
+            "qldpc_osd_destroy", "qldpc_cluster_create", "qldpc_cluster_decode_batch",
+            "qldpc_cluster_destroy")
+QLDPC_CLUSTER_SKIPPED = 0
+QLDPC_CLUSTER_DECODED = 1
+QLDPC_CLUSTER_TOO_LARGE = -1
+QLDPC_CLUSTER_TOO_MANY = -2
+QLDPC_CLUSTER_STALLED = -3
 QLDPC_OSD_SKIPPED = 0
 QLDPC_OSD_SOLVED = 1
 QLDPC_OSD_TOO_MANY = -1
@@ -60,6 +66,12 @@ class qldpc_relay_params(ctypes.Structure):
 class qldpc_osd_params(ctypes.Structure):
     _fields_ = [("bp_iters", ctypes.c_int32), ("llr_confident", ctypes.c_float),
                 ("max_candidates", ctypes.c_int32)]
+
+
+class qldpc_cluster_params(ctypes.Structure):
+    _fields_ = [("bp_iters", ctypes.c_int32), ("llr_accept", ctypes.c_float),
+                ("llr_erase", ctypes.c_float), ("max_clusters", ctypes.c_int32),
+                ("max_cluster_faults", ctypes.c_int32)]
 
 
 class qldpc_info(ctypes.Structure):
@@ -112,6 +124,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qldpc_osd_decode_batch.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P]
     lib.qldpc_osd_destroy.argtypes = [P]
     lib.qldpc_osd_destroy.restype = None
+    lib.qldpc_cluster_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, P, P,
+                                         P, ctypes.POINTER(qldpc_cluster_params), ctypes.c_int]
+    lib.qldpc_cluster_decode_batch.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P]
+    lib.qldpc_cluster_destroy.argtypes = [P]
+    lib.qldpc_cluster_destroy.restype = None
     lib.qldpc_soft_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, P, P, P,
                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int]
     lib.qldpc_soft_workspace_bytes.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
@@ -585,3 +602,91 @@ def first_leg_then_osd(first_leg: "RelayDecoder", osd: FilteredOSD, syndromes, s
     cor, _, conv, _ = first_leg.decode(syndromes, stream=stream)
     status, ncand = osd.decode(syndromes, cor, skip=conv, stream=stream)
     return cor, status, ncand, conv
+
+
+# ---- cluster decoder ------------------------------------------------------------------
+
+def qldpc_cluster_create(M, N, row_ptr, col_idx, priors, params: qldpc_cluster_params,
+                         device=0):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    pr = np.ascontiguousarray(priors, dtype=np.float64)
+    _check(lib.qldpc_cluster_create(ctypes.byref(h), int(M), int(N), rp.ctypes.data,
+                                    ci.ctypes.data, pr.ctypes.data, ctypes.byref(params),
+                                    int(device)), "qldpc_cluster_create")
+    return h
+
+
+def qldpc_cluster_decode_batch(h, syn_ptr, B, skip_ptr, cor_ptr, status_ptr, steps_ptr=None,
+                               stream=None):
+    _check(load_library().qldpc_cluster_decode_batch(h, syn_ptr, int(B), skip_ptr, cor_ptr,
+                                                     status_ptr, steps_ptr, stream),
+           "qldpc_cluster_decode_batch")
+
+
+def qldpc_cluster_destroy(h) -> None:
+    if h is not None and h.value:
+        load_library().qldpc_cluster_destroy(h)
+
+
+class ClusterDecoder:
+    """BP + generalized union-find cluster decoder for one decoding problem on one GPU
+    (paper Sec. 2.5 and Sec. 6)."""
+
+    def __init__(self, row_ptr, col_idx, priors, bp_iters: int = 25, llr_accept: float = -0.5,
+                 llr_erase: float = 4.5, max_clusters: int = 128,
+                 max_cluster_faults: int = 512, device: int = 0):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        self.M = row_ptr.size - 1
+        self.N = int(np.asarray(priors).size)
+        self.params = qldpc_cluster_params(bp_iters, llr_accept, llr_erase, max_clusters,
+                                           max_cluster_faults)
+        self.device = device
+        self.handle = qldpc_cluster_create(self.M, self.N, row_ptr, col_idx, priors,
+                                           self.params, device)
+        self.syndrome_words = (self.M + 63) // 64
+        self.correction_words = (self.N + 63) // 64
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            qldpc_cluster_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, syndromes, corrections, skip=None, status=None, steps=None, stream=None):
+        """Decode the shots with skip == 0 (all when skip is None).  syndromes int64
+        [B, ceil(M/64)] and corrections int64 [B, ceil(N/64)] (updated in place for decoded
+        shots) are CUDA tensors; returns (status int32 [B], steps int32 [B])."""
+        import torch
+        B = syndromes.shape[0]
+        if syndromes.shape != (B, self.syndrome_words) or not syndromes.is_contiguous():
+            raise ValueError("syndromes must be a contiguous CUDA tensor [B, ceil(M/64)]")
+        if corrections.shape != (B, self.correction_words) or not corrections.is_contiguous():
+            raise ValueError("corrections must be a contiguous CUDA tensor [B, ceil(N/64)]")
+        dev = syndromes.device
+        status = status if status is not None else torch.empty(B, dtype=torch.int32, device=dev)
+        steps = steps if steps is not None else torch.empty(B, dtype=torch.int32, device=dev)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        qldpc_cluster_decode_batch(self.handle, ctypes.c_void_p(syndromes.data_ptr()), B,
+                                   _vp(skip) if skip is not None else None,
+                                   ctypes.c_void_p(corrections.data_ptr()),
+                                   ctypes.c_void_p(status.data_ptr()),
+                                   ctypes.c_void_p(steps.data_ptr()),
+                                   ctypes.c_void_p(s.cuda_stream))
+        return status, steps
+
+
+def first_leg_then_cluster(first_leg: "RelayDecoder", cluster: ClusterDecoder, syndromes,
+                           stream=None):
+    """First Relay leg on every shot, BP + cluster decoding on the shots it leaves
+    unconverged (paper Sec. 7.1).  Returns (corrections, status, steps, converged)."""
+    cor, _, conv, _ = first_leg.decode(syndromes, stream=stream)
+    status, steps = cluster.decode(syndromes, cor, skip=conv, stream=stream)
+    return cor, status, steps, conv
