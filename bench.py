@@ -291,16 +291,40 @@ def run_decode_only(args):
     dec.close()
 
 
-def osd_variant(args, dev, stream, flush):
-    """First Relay leg + filtered-OSD (paper Sec. 5, Sec. 7.1) against full Relay on the
-    gross 12-round model at p = 0.02, where the first leg leaves about 1% of the shots
-    unconverged: the post-processor's time on those shots, its outcomes, and both
-    decoders' logical error rates on the same 10^5 shots."""
+def timed_post(post, syn, base_cor, skip, stream, flush, steps=3, warmup=3):
+    """CUDA-event ms of a post-processor launch (corrections reset before each)."""
+    import torch
+    cor = torch.empty_like(base_cor)
+    n = syn.shape[0]
+    status = torch.empty(n, dtype=torch.int32, device=syn.device)
+    extra = torch.empty(n, dtype=torch.int32, device=syn.device)
+    times = []
+    for k in range(warmup + steps):
+        cor.copy_(base_cor)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            post.decode(syn, cor, skip, status, extra, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= warmup:
+            times.append(e0.elapsed_time(e1))
+    return sum(times) / len(times), cor, status, extra
+
+
+def post_processing_variants(args, dev, stream, flush):
+    """First Relay leg + filtered-OSD (paper Sec. 5) and first Relay leg + BP + cluster
+    decoding (Sec. 2.5, Sec. 6), the paper's two post-processed decoders (Sec. 7.1),
+    against full Relay on the gross 12-round model at p = 0.02, where the first leg
+    leaves about 1% of the shots unconverged: each post-processor's time on those
+    shots, its outcomes, and the three decoders' logical error rates on the same 10^5
+    shots."""
     import torch
 
-    from paper_2511_21660_gb300 import (QLDPC_OSD_NO_SOLUTION, QLDPC_OSD_SOLVED,
-                                        QLDPC_OSD_TOO_MANY, FilteredOSD, RelayConfig,
-                                        RelayDecoder)
+    from paper_2511_21660_gb300 import (QLDPC_CLUSTER_DECODED, QLDPC_OSD_NO_SOLUTION,
+                                        QLDPC_OSD_SOLVED, QLDPC_OSD_TOO_MANY, ClusterDecoder,
+                                        FilteredOSD, RelayConfig, RelayDecoder)
     from workloads.torch_sampling import pack_bits_t, sample_faults_t, syndromes_t
     p, n, conf, rmax = 0.02, SHOTS, 8.0, 500
     P = phenomenological_dem(BB144, 12, p)
@@ -312,27 +336,16 @@ def osd_variant(args, dev, stream, flush):
     relay = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam,
                          RelayConfig(stop_after_solutions=S_SOLUTIONS), device=dev.index)
     osd = FilteredOSD(P.row_ptr, P.col_idx, P.p, 25, conf, rmax, device=dev.index)
+    accept, erase = -0.5, 4.5
+    cluster = ClusterDecoder(P.row_ptr, P.col_idx, P.p, 25, accept, erase, 4096, 512,
+                             device=dev.index)
     fo = first.outputs(n)
     ms_first = sum(timed_decode(first, syn, fo, 3, 3, stream, flush)) / 3
     ro = relay.outputs(n)
     ms_relay = sum(timed_decode(relay, syn, ro, 3, 2, stream, flush)) / 3
     skip = fo[2]
-    cor = torch.empty_like(fo[0])
-    status = torch.empty(n, dtype=torch.int32, device=dev)
-    ncand = torch.empty(n, dtype=torch.int32, device=dev)
-    times = []
-    for k in range(6):
-        cor.copy_(fo[0])
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            osd.decode(syn, cor, skip=skip, status=status, n_candidates=ncand, stream=stream)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        if k >= 3:
-            times.append(e0.elapsed_time(e1))
-    ms_osd = sum(times) / len(times)
+    ms_osd, cor, status, ncand = timed_post(osd, syn, fo[0], skip, stream, flush)
+    ms_cl, cor_cl, st_cl, steps_cl = timed_post(cluster, syn, fo[0], skip, stream, flush)
     A = torch.from_numpy(P.A.astype(np.float32)).to(dev)
     shifts = torch.arange(64, dtype=torch.int64, device=dev)
 
@@ -341,8 +354,10 @@ def osd_variant(args, dev, stream, flush):
         return ((F ^ bits).to(torch.float32) @ A.T).to(torch.int64).remainder(2).any(1)
     fail_first = (logical(cor) | ((skip == 0) & (status != QLDPC_OSD_SOLVED))).sum().item()
     fail_relay = (logical(ro[0]) | (ro[2] == 0)).sum().item()
+    fail_cl = (logical(cor_cl) | ((skip == 0) & (st_cl != QLDPC_CLUSTER_DECODED))).sum().item()
     todo = int((skip == 0).sum().item())
     st = status[skip == 0]
+    stc = st_cl[skip == 0]
     out = {"workload": "gross [[144,12,12]] phenomenological T=12, p=0.02, 10^5 shots",
            "osd": f"25 plain BP iterations, Lambda_confident={conf}, |R|_max={rmax}",
            "first_leg_ms": ms_first, "first_leg_failures": todo,
@@ -352,20 +367,41 @@ def osd_variant(args, dev, stream, flush):
                           "no_solution": int((st == QLDPC_OSD_NO_SOLUTION).sum().item())},
            "mean_candidates": float(ncand[skip == 0].float().mean().item()) if todo else 0.0,
            "ler_first_leg_plus_osd": fail_first / n, "ler_relay_S5": fail_relay / n,
-           "relay_ms": ms_relay}
+           "relay_ms": ms_relay,
+           "cluster": {"decoder": f"25 plain BP iterations, Lambda_accept={accept}, "
+                                  f"Lambda_erase={erase}, clusters <= 4096, "
+                                  f"interior faults <= 512",
+                       "ms": ms_cl,
+                       "shots_per_s": todo / (ms_cl / 1e3) if todo else None,
+                       "decoded": int((stc == QLDPC_CLUSTER_DECODED).sum().item()),
+                       "failed": int((stc < 0).sum().item()),
+                       "mean_growth_steps": float(steps_cl[skip == 0].float().mean().item())
+                       if todo else 0.0,
+                       "ler_first_leg_plus_cluster": fail_cl / n}}
     if args.cpu_baseline and todo:
         from oracle.osd import OSDParams, bp_llrs, filtered_osd
         idx = torch.nonzero(skip == 0).flatten()[:40].cpu().numpy()
         sig = syndromes_t(P.H, F[torch.from_numpy(idx).to(dev)]).cpu().numpy()
         t0 = time.perf_counter()
         L = bp_llrs(P.row_ptr, P.col_idx, P.p, sig, 25)
+        t_bp = time.perf_counter() - t0
         for b in range(sig.shape[0]):
             filtered_osd(P.H, sig[b], L[b], OSDParams(25, conf, rmax))
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": sig.shape[0] / dt, "unit": "post-processed shots/s",
                                "cores": os.cpu_count(), "kind": "oracle",
                                "sample": f"the first {sig.shape[0]} unconverged shots"}
-    for d in (first, relay, osd):
+    if args.cpu_baseline and todo:
+        from oracle.cluster import ClusterParams, bp_uf
+        t0 = time.perf_counter()
+        for b in range(sig.shape[0]):
+            bp_uf(P.H, sig[b], L[b], ClusterParams(25, accept, erase, 512, 4096))
+        dt = time.perf_counter() - t0 + t_bp
+        out["cluster"]["cpu_baseline"] = {
+            "value": sig.shape[0] / dt, "unit": "post-processed shots/s",
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the first {sig.shape[0]} unconverged shots"}
+    for d in (first, relay, osd, cluster):
         d.close()
     return out
 
@@ -495,7 +531,7 @@ def run_ours(args):
            "d2h_bytes_per_step": int(SHOTS * (cw * 8 + 4 + 1 + 4))}
     assert np.array_equal(h_cor.numpy(), out[0].cpu().numpy()), "host path differs"
 
-    variants["first_leg_then_filtered_osd"] = osd_variant(args, dev, stream, flush)
+    variants["first_leg_then_post_processing"] = post_processing_variants(args, dev, stream, flush)
     cpu = cpu_oracle_rate(P, sig, gam) if args.cpu_baseline else None
     clocks = clk.summary()
     line = {
