@@ -133,3 +133,43 @@ def test_first_leg_then_osd_pipeline_matches_oracle():
     assert (st[todo] == sto).all() and (nc[todo] == nco).all()
     assert (cor[todo] == Fo).all()
     assert (st[conv == 1] == QLDPC_OSD_SKIPPED).all()
+
+
+def test_full_size_post_processing_sampled_parity():
+    """The benchmark's post-processing workload: 10^5 gross shots at p = 0.02, first Relay
+    leg, then filtered-OSD and the cluster decoder on the unconverged shots; sampled
+    unconverged shots against the oracle."""
+    from oracle.cluster import ClusterParams, bp_uf
+    from paper_2511_21660_gb300 import ClusterDecoder
+    P = phenomenological_dem(BB144, 12, 0.02)
+    F, sig = _shots(P, 100000, 2)
+    g0 = gamma_table(P.N, 0, 0.125, -0.24, 0.66, 2)
+    first = RelayDecoder(P.row_ptr, P.col_idx, P.p, g0,
+                         RelayConfig(legs_after_first=0, stop_after_solutions=1))
+    osd = FilteredOSD(P.row_ptr, P.col_idx, P.p, 25, 8.0, 500)
+    cl = ClusterDecoder(P.row_ptr, P.col_idx, P.p, 25, -0.5, 4.5, 4096, 512)
+    syn = torch.from_numpy(pack_bits(sig).view(np.int64)).cuda()
+    cor, _, conv, _ = first.decode(syn)
+    cor_cl = cor.clone()
+    st, nc = osd.decode(syn, cor, skip=conv)
+    stc, steps = cl.decode(syn, cor_cl, skip=conv)
+    torch.cuda.synchronize()
+    conv = conv.cpu().numpy()
+    cor = unpack_bits(cor.cpu().numpy().view(np.uint64), P.N)
+    cor_cl = unpack_bits(cor_cl.cpu().numpy().view(np.uint64), P.N)
+    st, nc, stc, steps = (x.cpu().numpy() for x in (st, nc, stc, steps))
+    for d in (first, osd, cl):
+        d.close()
+    todo = np.nonzero(conv == 0)[0]
+    assert todo.size >= 300
+    pick = np.random.default_rng(1).choice(todo, 40, replace=False)
+    L = bp_llrs(P.row_ptr, P.col_idx, P.p, sig[pick], 25, precision="f32")
+    for k, b in enumerate(pick):
+        f, s_, n = filtered_osd(P.H, sig[b], L[k], OSDParams(25, 8.0, 500))
+        assert st[b] == s_ and nc[b] == n
+        if s_ == 1:
+            assert (cor[b] == f).all()
+        f, s_, n = bp_uf(P.H, sig[b], L[k], ClusterParams(25, -0.5, 4.5, 512, 4096))
+        assert stc[b] == s_ and steps[b] == n
+        if s_ == 1:
+            assert (cor_cl[b] == f).all()

@@ -204,18 +204,35 @@ def test_logical_error_rate_matches_fp64_oracle_code_capacity():
     assert (syndrome(P, got[0][ok]) == sig[ok]).all()
 
 
-def test_full_size_gross_batch_sampled_parity():
-    """10^5 gross-code shots in the benchmark's launch configuration."""
-    P = problem("bb144_T12")
-    F, sig = shots(P, 100000, 1)
-    gam = gamma_for(P, seed=1)
-    cfg = RelayConfig(stop_after_solutions=5)
+_FULL = {}
+
+
+def _full_size_inputs():
+    if not _FULL:
+        P = problem("bb144_T12")
+        F, sig = shots(P, 100000, 1)
+        _FULL["P"], _FULL["sig"], _FULL["gam"] = P, sig, gamma_for(P, seed=1)
+    return _FULL["P"], _FULL["sig"], _FULL["gam"]
+
+
+# every block shape the benchmark's autotuner chooses from, in both message precisions
+@pytest.mark.parametrize("prec,bt", [(QLDPC_MSG_FP32, b) for b in (256, 384, 512, 640, 768)]
+                         + [(QLDPC_MSG_FP16, b) for b in (384, 512)])
+def test_full_size_gross_batch_sampled_parity(prec, bt):
+    """10^5 gross-code shots in the benchmark's launch configurations."""
+    P, sig, gam = _full_size_inputs()
+    cfg = RelayConfig(stop_after_solutions=5, msg_precision=prec, block_threads=bt)
     cor, legs, conv, iters, info = gpu_decode(P, gam, sig, cfg)
+    assert info.block_threads == bt
     ok = conv == 1
     from workloads import syndromes_of
     assert (syndromes_of(P.row_ptr, P.col_idx, cor[ok]) == sig[ok]).all()
     rng = np.random.default_rng(0)
     pick = np.sort(rng.choice(sig.shape[0], 300, replace=False))
     pick = np.union1d(pick, np.argsort(iters)[-20:])     # include the slowest shots
-    ref = relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig[pick], _params(cfg), precision="f32")
-    assert_same_decisions((cor[pick], legs[pick], conv[pick], iters[pick]), ref, "full-size")
+    key = ("ref", PREC[prec], tuple(pick[:3]))
+    if key not in _FULL:
+        _FULL[key] = relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig[pick], _params(cfg),
+                                  precision=PREC[prec])
+    assert_same_decisions((cor[pick], legs[pick], conv[pick], iters[pick]), _FULL[key],
+                          f"full-size {bt}")
