@@ -97,13 +97,14 @@ __device__ __forceinline__ int swz(int i) {
 //           (warm_mode 0) or w (warm_mode 1); nu(0) = lambda(0)
 // bb holds (1 - gamma_j) * lambda_j(0), rounded, which is the first product of
 // the memory update and is constant within a leg.
-template <typename MT, int NT, int VPT, int DV>
+template <typename MT, int NT, int VPT, int DV, bool SKIP = false>
 __device__ __forceinline__ void leg_init(const FusedGraph &g, const DevParams &p, int leg,
                                          unsigned char *msg, const float *ws, float (&Lam)[VPT],
                                          float (&bb)[VPT], float (&gg)[VPT]) {
     const float *grow = g.gamma + (size_t)leg * g.N;
 #pragma unroll
     for (int r = 0; r < VPT; ++r) {
+        if (SKIP && r * NT >= g.N) break;  // the block's remaining fault slots are empty
         const int j = threadIdx.x + r * NT;
         if (j < g.N) {
             const float lam0 = canon((leg == 0 || p.warm_mode == 1) ? ws[j] : Lam[r]);
@@ -297,7 +298,7 @@ __device__ __forceinline__ float fault_update(unsigned char *msg, const int (&sl
 // bitmap fw, and the syndrome of the decision: every fault with F_j = 1 flips the
 // parity bits of its checks in par (zeroed by the preceding check pass).  Decisions
 // are sparse, so this costs a few atomics per shot instead of a pass over all edges.
-template <typename MT, int NT, int VPT, int DV>
+template <typename MT, int NT, int VPT, int DV, bool SKIP = false>
 __device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *msg, uint32_t *fw,
                                            uint32_t *par, float (&Lam)[VPT],
                                            const float (&bb)[VPT], const float (&gg)[VPT],
@@ -307,6 +308,7 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *m
     uint32_t dmask = 0u;  // bit r: this thread's fault r is decided (F_j = 1)
 #pragma unroll
     for (int r = 0; r < VPT; ++r) {
+        if (SKIP && r * NT >= g.N) break;  // the block's remaining fault slots are empty
         const int j = threadIdx.x + r * NT;
         const bool valid = j < g.N;
         float L = 0.0f;
@@ -350,12 +352,13 @@ __device__ __forceinline__ bool warp_converged(const uint32_t *par, const uint32
 // over the warp; lane 0 stores the warp's partial in part[warp].  After a barrier
 // every thread adds the NT/32 partials: integer addition makes the total exact and
 // independent of the order.
-template <int NT, int VPT>
+template <int NT, int VPT, bool SKIP = false>
 __device__ __forceinline__ void warp_weight(const FusedGraph &g, const float *ws,
                                             const float (&Lam)[VPT], long long *part) {
     long long s = 0;
 #pragma unroll
     for (int r = 0; r < VPT; ++r) {
+        if (SKIP && r * NT >= g.N) break;
         const int j = threadIdx.x + r * NT;
         if (j < g.N && Lam[r] < 0.0f) s += wfix(ws[j]);
     }

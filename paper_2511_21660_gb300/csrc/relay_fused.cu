@@ -37,7 +37,9 @@ namespace {
 // iteration: check pass | barrier | fault pass | barrier | per-warp convergence
 // test.  A leg end adds the weight reduction, the next leg's initialisation and one
 // barrier.  Called by every thread of the block with block-uniform arguments.
-template <typename MT, int NT, int VPT, int DC, int DV>
+// SKIP: the shot's code may use only part of the block's fault slots (mixed batches),
+// so the per-fault loops stop at the code's last slot.
+template <typename MT, int NT, int VPT, int DC, int DV, bool SKIP = false>
 __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams &p, int shot,
                                             const uint64_t *sy, uint64_t *cor, DecodeOut out,
                                             unsigned char *msg, uint32_t *fw, uint32_t *fb,
@@ -51,13 +53,13 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
     int leg = 0, sols = 0, t = 0, pb = 0;
     long long iters = 0, Wbest = 0;
     bool have = false;
-    leg_init<MT, NT, VPT, DV>(g, p, 0, msg, ws, Lam, bb, gg);
+    leg_init<MT, NT, VPT, DV, SKIP>(g, p, 0, msg, ws, Lam, bb, gg);
     __syncthreads();
     for (;;) {
         uint32_t *pc = par + pb * g.m_words;
         check_pass<NT, DC>(g, reinterpret_cast<MT *>(msg), sg, pc, C);
         __syncthreads();
-        fault_pass<MT, NT, VPT, DV>(g, msg, fw, pc, Lam, bb, gg, C);
+        fault_pass<MT, NT, VPT, DV, SKIP>(g, msg, fw, pc, Lam, bb, gg, C);
         __syncthreads();
         ++iters;
         ++t;
@@ -69,12 +71,12 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
         // a solution equal to the kept one has its weight and cannot replace it
         const bool fresh = conv && !(have && warp_same_solution(fw, fb, 2 * g.cor_words));
         if (conv) ++sols;
-        if (fresh) warp_weight<NT, VPT>(g, ws, Lam, s_Wpart);
+        if (fresh) warp_weight<NT, VPT, SKIP>(g, ws, Lam, s_Wpart);
         const bool done = sols >= p.S || leg == p.R || spent;
         if (!done) {
             ++leg;
             t = 0;
-            leg_init<MT, NT, VPT, DV>(g, p, leg, msg, ws, Lam, bb, gg);
+            leg_init<MT, NT, VPT, DV, SKIP>(g, p, leg, msg, ws, Lam, bb, gg);
         }
         __syncthreads();  // the weight and the next leg's initial messages are visible
         if (fresh) {
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode_multi(MultiTable tab,
             cur = code;
             __syncthreads();
         }
-        decode_shot<MT, NT, VPT, DC, DV>(s_g, s_p, shot, syn + (size_t)shot * syn_stride,
+        decode_shot<MT, NT, VPT, DC, DV, true>(s_g, s_p, shot, syn + (size_t)shot * syn_stride,
                                          out.corr + (size_t)shot * cor_stride, out, msg, fw, fb,
                                          sg, par, ws, s_Wpart, Lam, bb, gg);
     }
