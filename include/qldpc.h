@@ -146,6 +146,25 @@ int qldpc_decode_batch_multi(qldpc_decoder *const *decoders, int32_t n_codes,
                              int32_t *iters, void *stream);
 
 /*
+ * The same mixed batch decoded per code: the shots are sorted into one index list per
+ * code on the device, then each code's shots run in one persistent launch of that
+ * decoder's own kernel shape (largest code first), all on `stream` (capturable in a
+ * CUDA graph).  Results equal qldpc_decode_batch_multi's.  Decoders may differ in
+ * message precision and degree family but must be distinct and on one device; each
+ * decoder's work counter is used.  workspace: device memory of at least
+ * qldpc_grouped_workspace_bytes(n_codes, B) bytes, caller-owned, not touched by other
+ * work meanwhile.  Errors: INVALID_ARG, UNSUPPORTED (baseline decoders, two devices),
+ * CUDA.
+ */
+uint64_t qldpc_grouped_workspace_bytes(int32_t n_codes, int64_t B);
+int qldpc_decode_batch_grouped(qldpc_decoder *const *decoders, int32_t n_codes,
+                               const int32_t *code_of_shot, const uint64_t *syndromes,
+                               int32_t syndrome_stride, int64_t B, uint64_t *corrections,
+                               int32_t correction_stride, int32_t *legs_used,
+                               uint8_t *converged, int32_t *iters, void *workspace,
+                               uint64_t workspace_bytes, void *stream);
+
+/*
  * Size of the static scratch area used by qldpc_decode_batch_host_static: 8 MiB of
  * device memory that every GPU loading this library holds until the process exits.
  */

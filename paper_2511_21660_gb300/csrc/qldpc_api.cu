@@ -324,7 +324,8 @@ int launch(qldpc_decoder *d, const uint64_t *syn, int64_t B, DecodeOut out, cuda
     QL_CUDA(cudaMemsetAsync(d->counter, 0, sizeof(unsigned int), st));
     const int grid = (int)std::min<int64_t>(d->grid, B);
     QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, syn, (int)B, out,
-                                 d->counter));
+                                 d->counter, ShotMap{nullptr, nullptr, d->fg.syn_words,
+                                                     d->fg.cor_words}));
     return QLDPC_OK;
 }
 
@@ -528,7 +529,7 @@ extern "C" int qldpc_decode_batch_host_static(qldpc_decoder *d, const uint64_t *
     QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, dsyn, (int)B,
                                  DecodeOut{dcor, legs_used ? dlegs : nullptr,
                                            converged ? dconv : nullptr, iters ? diters : nullptr},
-                                 counter));
+                                 counter, ShotMap{nullptr, nullptr, sw, cw}));
     QL_CUDA(cudaMemcpyAsync(corrections, dcor, 8 * (size_t)cw * B, cudaMemcpyDeviceToHost, st));
     if (legs_used) QL_CUDA(cudaMemcpyAsync(legs_used, dlegs, 4 * (size_t)B, cudaMemcpyDeviceToHost, st));
     if (iters) QL_CUDA(cudaMemcpyAsync(iters, diters, 4 * (size_t)B, cudaMemcpyDeviceToHost, st));
@@ -598,6 +599,105 @@ int qldpc_decode_batch_multi(qldpc_decoder *const *decoders, int32_t n_codes,
     QL_CUDA(fk->launch_multi(dim3(grid), smem, st, tab, code_of_shot, syndromes, syndrome_stride,
                              correction_stride, (int)B,
                              DecodeOut{corrections, legs_used, converged, iters}, d0->counter));
+    return QLDPC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Shots of a mixed batch sorted into one index list per code ([n_codes][B], in any
+// order within a code; counts[c] = length of list c).  Shots with an unknown code id
+// get legs 0, converged 0 and iters -1, as in the single-launch mixed kernel.
+__global__ void partition_shots(const int32_t *__restrict__ code_of_shot, int B, int n_codes,
+                                int32_t *counts, int32_t *lists, DecodeOut out) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        const int c = code_of_shot[b];
+        if (c >= 0 && c < n_codes) {
+            const int k = atomicAdd(counts + c, 1);
+            lists[(size_t)c * B + k] = b;
+        } else {
+            if (out.legs) out.legs[b] = 0;
+            if (out.conv) out.conv[b] = 0;
+            if (out.iters) out.iters[b] = -1;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t qldpc_grouped_workspace_bytes(int32_t n_codes, int64_t B) {
+    if (n_codes < 1 || B < 0) return 0;
+    return (uint64_t)align_up(sizeof(int32_t) * (size_t)n_codes, 256) +
+           sizeof(int32_t) * (uint64_t)n_codes * (uint64_t)B;
+}
+
+int qldpc_decode_batch_grouped(qldpc_decoder *const *decoders, int32_t n_codes,
+                               const int32_t *code_of_shot, const uint64_t *syndromes,
+                               int32_t syndrome_stride, int64_t B, uint64_t *corrections,
+                               int32_t correction_stride, int32_t *legs_used,
+                               uint8_t *converged, int32_t *iters, void *workspace,
+                               uint64_t workspace_bytes, void *stream) {
+    g_last_error.clear();
+    if (!decoders || n_codes < 1 || n_codes > kMaxMultiCodes)
+        return fail(QLDPC_ERR_INVALID_ARG, "need 1..%d decoders", kMaxMultiCodes);
+    if (B < 0 || B > 0x7fffffffLL) return fail(QLDPC_ERR_INVALID_ARG, "batch size out of range");
+    if (B == 0) return QLDPC_OK;
+    if (!code_of_shot || !syndromes || !corrections || !workspace)
+        return fail(QLDPC_ERR_INVALID_ARG,
+                    "code_of_shot, syndromes, corrections and workspace are required");
+    if (workspace_bytes < qldpc_grouped_workspace_bytes(n_codes, B))
+        return fail(QLDPC_ERR_INVALID_ARG, "workspace of %llu bytes below the %llu needed",
+                    (unsigned long long)workspace_bytes,
+                    (unsigned long long)qldpc_grouped_workspace_bytes(n_codes, B));
+    const qldpc_decoder *d0 = decoders[0];
+    for (int c = 0; c < n_codes; ++c) {
+        const qldpc_decoder *d = decoders[c];
+        if (!d) return fail(QLDPC_ERR_INVALID_ARG, "decoder %d is NULL", c);
+        if (d->kernel != QLDPC_KERNEL_FUSED)
+            return fail(QLDPC_ERR_UNSUPPORTED, "grouped batches need fused-kernel decoders");
+        if (d->device != d0->device)
+            return fail(QLDPC_ERR_UNSUPPORTED, "decoders of a batch must share the device");
+        for (int c2 = 0; c2 < c; ++c2)
+            if (decoders[c2] == d)
+                return fail(QLDPC_ERR_INVALID_ARG, "decoder %d appears twice", c);
+        if (syndrome_stride < d->fg.syn_words || correction_stride < d->fg.cor_words)
+            return fail(QLDPC_ERR_INVALID_ARG, "row strides %d/%d below code %d's %d/%d words",
+                        syndrome_stride, correction_stride, c, d->fg.syn_words, d->fg.cor_words);
+    }
+    DeviceGuard guard(d0->device);
+    QL_CUDA(guard.err);
+    const void *ptrs[7] = {code_of_shot, syndromes, corrections, legs_used, converged, iters,
+                           workspace};
+    for (int q = 0; q < 7; ++q)
+        if (ptrs[q] && !is_device_ptr(ptrs[q]))
+            return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t *counts = static_cast<int32_t *>(workspace);
+    int32_t *lists = reinterpret_cast<int32_t *>(static_cast<char *>(workspace) +
+                                                 align_up(sizeof(int32_t) * n_codes, 256));
+    const DecodeOut out{corrections, legs_used, converged, iters};
+    QL_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_codes, st));
+    const int pgrid = (int)std::min<int64_t>((B + 255) / 256, (int64_t)d0->num_sms * 8);
+    partition_shots<<<pgrid, 256, 0, st>>>(code_of_shot, (int)B, n_codes, counts, lists, out);
+    QL_CUDA(cudaGetLastError());
+    // each code with its own kernel shape, largest code first
+    int order[kMaxMultiCodes];
+    for (int c = 0; c < n_codes; ++c) order[c] = c;
+    std::sort(order, order + n_codes,
+              [&](int a, int b) { return decoders[a]->fg.E > decoders[b]->fg.E; });
+    for (int q = 0; q < n_codes; ++q) {
+        const int c = order[q];
+        qldpc_decoder *d = decoders[c];
+        QL_CUDA(cudaMemsetAsync(d->counter, 0, sizeof(unsigned int), st));
+        const int grid = (int)std::min<int64_t>(d->grid, B);
+        QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, syndromes, (int)B,
+                                     out, d->counter,
+                                     ShotMap{lists + (size_t)c * B, counts + c, syndrome_stride,
+                                             correction_stride}));
+    }
     return QLDPC_OK;
 }
 

@@ -68,6 +68,15 @@ struct DecodeOut {
     int32_t *iters;
 };
 
+// Which shots a decode launch takes: all B in order (order == nullptr), or the *count
+// shots order[0..*count) of a batch; rows of the syndrome / correction arrays are
+// syn_stride / cor_stride 64-bit words apart.
+struct ShotMap {
+    const int32_t *order;
+    const int32_t *count;
+    int syn_stride, cor_stride;
+};
+
 // One compiled instance of the fused kernel.
 struct FusedKernel {
     int msg_fp16;   // 0 float32 storage, 1 binary16 storage
@@ -78,7 +87,7 @@ struct FusedKernel {
     const void *decode_fn;   // __global__ symbol of the decode kernel
     cudaError_t (*launch_decode)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                                  const DevParams &p, const uint64_t *syn, int B, DecodeOut out,
-                                 unsigned int *counter);
+                                 unsigned int *counter, ShotMap map);
     const void *multi_fn;    // __global__ symbol of the mixed-batch kernel
     cudaError_t (*launch_multi)(dim3 grid, size_t smem, cudaStream_t st, const MultiTable &tab,
                                 const int32_t *code_of_shot, const uint64_t *syn,

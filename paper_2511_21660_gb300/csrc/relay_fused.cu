@@ -97,11 +97,13 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
     }
 }
 
-// One block per shot at a time; shots come from a global counter.
+// One block per shot at a time; shots come from a global counter (through the shot
+// map's index list when it has one).
 template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
 __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams p,
                                                    const uint64_t *__restrict__ syn, int B,
-                                                   DecodeOut out, unsigned int *counter) {
+                                                   DecodeOut out, unsigned int *counter,
+                                                   ShotMap map) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *msg = smem_raw;
     uint32_t *fw, *fb, *sg, *par;
@@ -115,14 +117,18 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
 #pragma unroll
     for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
 
+    const int limit = map.order ? min(*map.count, B) : B;
     for (;;) {
         __syncthreads();  // the previous shot is done with shared memory and s_shot
-        if (threadIdx.x == 0) s_shot = (int)atomicAdd(counter, 1u);
+        if (threadIdx.x == 0) {
+            const int k = (int)atomicAdd(counter, 1u);
+            s_shot = k < limit ? (map.order ? map.order[k] : k) : -1;
+        }
         __syncthreads();
         const int shot = s_shot;
-        if (shot >= B) break;
-        decode_shot<MT, NT, VPT, DC, DV>(g, p, shot, syn + (size_t)shot * g.syn_words,
-                                         out.corr + (size_t)shot * g.cor_words, out, msg, fw,
+        if (shot < 0) break;
+        decode_shot<MT, NT, VPT, DC, DV>(g, p, shot, syn + (size_t)shot * map.syn_stride,
+                                         out.corr + (size_t)shot * map.cor_stride, out, msg, fw,
                                          fb, sg, par, ws, s_Wpart, Lam, bb, gg);
     }
 }
@@ -238,8 +244,9 @@ __global__ void __launch_bounds__(NT) fused_trace(FusedGraph g, DevParams p,
 template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
 cudaError_t launch_decode(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                           const DevParams &p, const uint64_t *syn, int B, DecodeOut out,
-                          unsigned int *counter) {
-    fused_decode<MT, NT, VPT, MINB, DC, DV><<<grid, NT, smem, st>>>(g, p, syn, B, out, counter);
+                          unsigned int *counter, ShotMap map) {
+    fused_decode<MT, NT, VPT, MINB, DC, DV><<<grid, NT, smem, st>>>(g, p, syn, B, out, counter,
+                                                                    map);
     return cudaGetLastError();
 }
 

@@ -32,7 +32,8 @@ EXPORTED = ("qldpc_create", "qldpc_decode_batch", "qldpc_decode_batch_host",
             "qldpc_soft_workspace_bytes", "qldpc_soft_forward", "qldpc_soft_backward",
             "qldpc_soft_destroy", "qldpc_osd_create", "qldpc_osd_decode_batch",
             "qldpc_osd_destroy", "qldpc_cluster_create", "qldpc_cluster_decode_batch",
-            "qldpc_cluster_destroy")
+            "qldpc_cluster_destroy", "qldpc_grouped_workspace_bytes",
+            "qldpc_decode_batch_grouped")
 QLDPC_CLUSTER_SKIPPED = 0
 QLDPC_CLUSTER_DECODED = 1
 QLDPC_CLUSTER_TOO_LARGE = -1
@@ -111,6 +112,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qldpc_decode_batch_host_static.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
     lib.qldpc_decode_batch_multi.argtypes = [P, ctypes.c_int32, P, P, ctypes.c_int32,
                                              ctypes.c_int64, P, ctypes.c_int32, P, P, P, P]
+    lib.qldpc_grouped_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    lib.qldpc_grouped_workspace_bytes.restype = ctypes.c_uint64
+    lib.qldpc_decode_batch_grouped.argtypes = [P, ctypes.c_int32, P, P, ctypes.c_int32,
+                                               ctypes.c_int64, P, ctypes.c_int32, P, P, P, P,
+                                               ctypes.c_uint64, P]
     lib.qldpc_trace_first_leg.argtypes = [P, P, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
     lib.qldpc_get_info.argtypes = [P, ctypes.POINTER(qldpc_info)]
     lib.qldpc_destroy.argtypes = [P]
@@ -218,6 +224,46 @@ def decode_mixed(decoders, code_of_shot, syndromes, stream=None):
                              ctypes.c_void_p(syndromes.data_ptr()), syndromes.shape[1], B,
                              ctypes.c_void_p(cor.data_ptr()), cw, ctypes.c_void_p(legs.data_ptr()),
                              ctypes.c_void_p(conv.data_ptr()), ctypes.c_void_p(iters.data_ptr()), st)
+    return cor, legs, conv, iters
+
+
+def qldpc_grouped_workspace_bytes(n_codes, B) -> int:
+    return int(load_library().qldpc_grouped_workspace_bytes(int(n_codes), int(B)))
+
+
+def qldpc_decode_batch_grouped(handles, code_ptr, syn_ptr, syn_stride, B, cor_ptr, cor_stride,
+                               legs_ptr, conv_ptr, iters_ptr, ws_ptr, ws_bytes, stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    _check(load_library().qldpc_decode_batch_grouped(arr, len(handles), code_ptr, syn_ptr,
+                                                     int(syn_stride), int(B), cor_ptr,
+                                                     int(cor_stride), legs_ptr, conv_ptr,
+                                                     iters_ptr, ws_ptr, int(ws_bytes), stream),
+           "qldpc_decode_batch_grouped")
+
+
+def decode_grouped(decoders, code_of_shot, syndromes, workspace=None, stream=None):
+    """Mixed batch decoded per code with each decoder's own kernel shape (arguments and
+    results as decode_mixed; `workspace` is a uint8 CUDA tensor of at least
+    qldpc_grouped_workspace_bytes(len(decoders), B) bytes, allocated when None)."""
+    import torch
+    B = syndromes.shape[0]
+    cw = max(d.correction_words for d in decoders)
+    dev = syndromes.device
+    need = qldpc_grouped_workspace_bytes(len(decoders), B)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    cor = torch.zeros((B, cw), dtype=torch.int64, device=dev)
+    legs = torch.empty(B, dtype=torch.int32, device=dev)
+    conv = torch.empty(B, dtype=torch.uint8, device=dev)
+    iters = torch.empty(B, dtype=torch.int32, device=dev)
+    st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    qldpc_decode_batch_grouped([d.handle for d in decoders],
+                               ctypes.c_void_p(code_of_shot.data_ptr()),
+                               ctypes.c_void_p(syndromes.data_ptr()), syndromes.shape[1], B,
+                               ctypes.c_void_p(cor.data_ptr()), cw,
+                               ctypes.c_void_p(legs.data_ptr()), ctypes.c_void_p(conv.data_ptr()),
+                               ctypes.c_void_p(iters.data_ptr()),
+                               ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), st)
     return cor, legs, conv, iters
 
 
