@@ -325,6 +325,7 @@ def post_processing_variants(args, dev, stream, flush):
     from paper_2511_21660_gb300 import (QLDPC_CLUSTER_DECODED, QLDPC_OSD_NO_SOLUTION,
                                         QLDPC_OSD_SOLVED, QLDPC_OSD_TOO_MANY, ClusterDecoder,
                                         FilteredOSD, RelayConfig, RelayDecoder)
+    from paper_2511_21660_gb300 import latency_tail
     from workloads.torch_sampling import pack_bits_t, sample_faults_t, syndromes_t
     p, n, conf, rmax = 0.02, SHOTS, 8.0, 500
     P = phenomenological_dem(BB144, 12, p)
@@ -368,6 +369,12 @@ def post_processing_variants(args, dev, stream, flush):
            "mean_candidates": float(ncand[skip == 0].float().mean().item()) if todo else 0.0,
            "ler_first_leg_plus_osd": fail_first / n, "ler_relay_S5": fail_relay / n,
            "relay_ms": ms_relay,
+           # Sec. 2.2 / 7.2 conditions on full Relay's measured iteration counts at this
+           # noise rate, in FPGA cycles at 2 per iteration (T_ref 500, T_gen 1000, 6000)
+           "relay_latency_tail": {k: v for k, v in latency_tail.report(
+               ro[3].cpu().numpy(), t_ref=500, t_gen=1000, t_max=6000, C=10,
+               cycles_per_iter=2).items()
+               if k in ("eps", "L", "holds", "max_code_blocks", "slowdown_bound")},
            "cluster": {"decoder": f"25 plain BP iterations, Lambda_accept={accept}, "
                                   f"Lambda_erase={erase}, clusters <= 4096, "
                                   f"interior faults <= 512",
@@ -531,6 +538,60 @@ def mixed_batch_variant(args, dev, stream, flush):
             "separate_total_ms": sum(v["ms"] for v in alone.values())}
 
 
+def soft_dmem_variant(args, dev, stream, flush):
+    """One training step of the differentiable leg: unrolled soft DMem-BP (25 iterations,
+    trainable gamma_j and alpha_t, BCE loss, checkpoints every 5 iterations, float32) on
+    a batch of 4096 gross T=12 shots at p = 0.003: forward and adjoint times."""
+    import torch
+
+    from paper_2511_21660_gb300 import SoftDMem
+    from workloads.torch_sampling import pack_bits_t, sample_faults_t, syndromes_t
+    P = phenomenological_dem(BB144, 12, 0.003)
+    B, T = 4096, 25
+    F = sample_faults_t(P.p, 20, B, device=dev)
+    syn = pack_bits_t(syndromes_t(P.H, F))
+    faults = pack_bits_t(F)
+    soft = SoftDMem(P.row_ptr, P.col_idx, P.p, T, 5, torch.float32, device=dev.index)
+    gamma = torch.full((P.N,), 0.125, dtype=torch.float32, device=dev)
+    alpha = torch.ones(T, dtype=torch.float32, device=dev)
+    ws = soft.workspace(B)
+    fwd, bwd = [], []
+    for k in range(8):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            e[0].record(stream)
+            loss, _, _ = soft.forward(syn, faults, gamma, alpha, ws, stream=stream)
+            e[1].record(stream)
+            gg, ga = soft.backward(syn, faults, gamma, alpha, ws, stream=stream)
+            e[2].record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            fwd.append(e[0].elapsed_time(e[1]))
+            bwd.append(e[1].elapsed_time(e[2]))
+    f_ms, b_ms = sum(fwd) / len(fwd), sum(bwd) / len(bwd)
+    out = {"workload": "gross T=12 p=0.003, batch 4096, 25 iterations, checkpoint every 5, "
+                       "float32, gamma_j (2736) and alpha_t (25) trainable",
+           "forward_ms": f_ms, "backward_ms": b_ms,
+           "step_shots_per_s": B / ((f_ms + b_ms) / 1e3),
+           "forward_edge_iterations_per_s": B * T * P.E / (f_ms / 1e3),
+           "loss": float(loss.item()),
+           "grad_gamma_norm": float(gg.norm().item())}
+    if args.cpu_baseline:
+        from oracle.soft import soft_dmem
+        n = 64
+        sig = syndromes_t(P.H, F[:n]).cpu().numpy()
+        Fh = F[:n].cpu().numpy()
+        t0 = time.perf_counter()
+        soft_dmem(P.row_ptr, P.col_idx, P.p, np.full(P.N, 0.125), np.ones(T), sig, Fh)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n / dt, "unit": "shots/s (forward + gradient)",
+                               "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"{n} shots, FP64, full trajectory stored"}
+    soft.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -658,6 +719,7 @@ def run_ours(args):
 
     variants["first_leg_then_post_processing"] = post_processing_variants(args, dev, stream, flush)
     variants["mixed_batch"] = mixed_batch_variant(args, dev, stream, flush)
+    variants["soft_dmem_training_step"] = soft_dmem_variant(args, dev, stream, flush)
     cpu = cpu_oracle_rate(P, sig, gam) if args.cpu_baseline else None
     clocks = clk.summary()
     line = {
