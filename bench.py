@@ -212,6 +212,21 @@ def kernel_source_sha1() -> str:
     return h.hexdigest()[:12]
 
 
+def profile_field(name: str):
+    """A value recorded in the committed ncu summary of the decode kernel, or None when
+    the summary is absent or was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "fused_decode_gross_T12.md")
+    if not os.path.exists(path):
+        return None
+    same, val = False, None
+    for line in open(path):
+        if line.startswith("| kernel source sha1"):
+            same = line.split("|")[2].strip() == kernel_source_sha1()
+        elif line.startswith(f"| {name} |"):
+            val = float(line.split("|")[2])
+    return val if same else None
+
+
 def traffic_per_launch(args):
     """DRAM bytes (read + write) of one decode launch, from the committed ncu summary.
 
@@ -665,7 +680,11 @@ def run_ours(args):
                                f"= {alg_ops / 1e9:.1f} G ops per launch",
                 "smem_message_bytes_per_launch": smem_bytes,
                 "smem_GBps": smem_bytes / (ms / 1e3) / 1e9,
-                "smem_peak_GBps": 128 * sms * 2070e6 / 1e9}
+                "smem_peak_GBps": 128 * sms * 2070e6 / 1e9,
+                # executed-instruction view from the same ncu summary: the fraction of
+                # issue slots used (the kernel is issue-bound; null if the summary is stale)
+                "issue_slots_used_frac": (lambda v: v / 100.0 if v is not None else None)(
+                    profile_field("smsp__issue_active.avg.pct_of_peak_sustained_active"))}
 
     # variants measured in the same run: FP16 messages and the plain baseline kernel
     variants = {}
