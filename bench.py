@@ -459,7 +459,7 @@ def mixed_batch_variant(args, dev, stream, flush):
     cfg = RelayConfig(stop_after_solutions=S_SOLUTIONS)
     timings = {}
     best = None
-    for bt in CANDIDATES + (1024,):
+    for bt in CANDIDATES:
         try:
             big = RelayDecoder(probs[2].row_ptr, probs[2].col_idx, probs[2].p, gams[2],
                                RelayConfig(stop_after_solutions=S_SOLUTIONS, block_threads=bt),

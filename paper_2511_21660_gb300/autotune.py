@@ -13,7 +13,7 @@ import os
 
 from .qldpc import QldpcError, RelayConfig, RelayDecoder
 
-CANDIDATES = (256, 384, 512, 640, 768)
+CANDIDATES = (256, 384, 512, 640, 768, 1024)
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "qldpc", "tuning.json")
 
 

@@ -317,6 +317,7 @@ void QL_EXPAND(QL_P, QL_DC, QL_DV)(const FusedKernel **out, int *n) {
         entry<384, 8, 3, false>(),
         entry<640, 5, 2, false>(),
         entry<768, 4, 2, false>(),
+        entry<1024, 8, 1, false>(),
         entry<512, 16, 1, false>(),
         entry<512, 32, 1, true>(),
     };

@@ -216,7 +216,8 @@ def _full_size_inputs():
 
 
 # every block shape the benchmark's autotuner chooses from, in both message precisions
-@pytest.mark.parametrize("prec,bt", [(QLDPC_MSG_FP32, b) for b in (256, 384, 512, 640, 768)]
+@pytest.mark.parametrize("prec,bt",
+                         [(QLDPC_MSG_FP32, b) for b in (256, 384, 512, 640, 768, 1024)]
                          + [(QLDPC_MSG_FP16, b) for b in (384, 512)])
 def test_full_size_gross_batch_sampled_parity(prec, bt):
     """10^5 gross-code shots in the benchmark's launch configurations."""
