@@ -258,19 +258,29 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
                         if (!cl[k]) Pb[k] = mb * at * s2 / (T(1) - P[k] * P[k]);
                     }
                 }
+                // tau_bar_k = sum_{m != k} Pb_m prod_{l != m, k} tau_l in O(d), without
+                // division: with pre_k = prod_{l < k} tau_l and suf_k = prod_{l > k} tau_l,
+                // the terms m > k are pre_k X_k and the terms m < k are Y_k suf_k, where
+                // X_k = Pb_{k+1} suf_{k+1} + tau_{k+1} X_{k+1} and
+                // Y_k = Pb_{k-1} pre_{k-1} + tau_{k-1} Y_{k-1}.
+                T pre[DCM], suf[DCM];
+                pre[0] = T(1);
+#pragma unroll
+                for (int k = 1; k < DCM; ++k) pre[k] = pre[k - 1] * tau[k - 1];
+                suf[DCM - 1] = T(1);
+#pragma unroll
+                for (int k = DCM - 2; k >= 0; --k) suf[k] = suf[k + 1] * tau[k + 1];
+                // slots k >= d hold tau = 1 and Pb = 0, so the full-width recurrences give
+                // the row's values for k < d
+                T X[DCM], Y = T(0);
+                X[DCM - 1] = T(0);
+#pragma unroll
+                for (int k = DCM - 2; k >= 0; --k) X[k] = Pb[k + 1] * suf[k + 1] + tau[k + 1] * X[k + 1];
 #pragma unroll
                 for (int k = 0; k < DCM; ++k) {
+                    if (k > 0) Y = Pb[k - 1] * pre[k - 1] + tau[k - 1] * Y;
                     if (k < d) {
-                        T tb = 0;
-#pragma unroll
-                        for (int m = 0; m < DCM; ++m) {
-                            if (m == k || m >= d) continue;
-                            T rest = Pb[m];
-#pragma unroll
-                            for (int l = 0; l < DCM; ++l)
-                                if (l != m && l != k && l < d) rest *= tau[l];
-                            tb += rest;
-                        }
+                        const T tb = pre[k] * X[k] + Y * suf[k];
                         nb[e0 + k] = inner ? tb * (T(1) - tau[k] * tau[k]) / T(2) : T(0);
                     }
                 }
