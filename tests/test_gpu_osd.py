@@ -173,3 +173,42 @@ def test_full_size_post_processing_sampled_parity():
         assert stc[b] == s_ and steps[b] == n
         if s_ == 1:
             assert (cor_cl[b] == f).all()
+
+
+@pytest.mark.parametrize("dc_wide", [(9, 17), (17, 33)])
+def test_osd_and_cluster_on_wider_check_families(dc_wide):
+    """Random graphs whose widest checks put them in the 16- and 32-slot families."""
+    from oracle.cluster import ClusterParams, bp_uf
+    from paper_2511_21660_gb300 import ClusterDecoder
+    from workloads import DecodingProblem
+    rng = np.random.default_rng(31 + dc_wide[0])
+    M, N = 150, 300
+    H = np.zeros((M, N), dtype=np.uint8)
+    for j in range(N):
+        H[rng.choice(M, int(rng.integers(1, 5)), replace=False), j] = 1
+    for i in rng.choice(M, 6, replace=False):
+        H[i, :] = 0
+        free = np.nonzero(H.sum(0) < 4)[0]
+        H[i, rng.choice(free, int(rng.integers(*dc_wide)), replace=False)] = 1
+    assert dc_wide[0] <= H.sum(1).max() < dc_wide[1]
+    p = rng.uniform(0.01, 0.08, N)
+    P = DecodingProblem("wide", H, np.zeros((1, N), np.uint8), p, {"code": "bb72"})
+    F = (rng.random((60, N)) < p).astype(np.uint8)
+    sig = ((F.astype(np.int64) @ H.T.astype(np.int64)) % 2).astype(np.uint8)
+    prm = OSDParams(25, 4.0, 300)
+    _assert_same(_gpu_osd(P, sig, prm), _oracle_osd(P, sig, prm), f"osd {dc_wide}")
+    cp = ClusterParams(25, -0.5, 3.0, 512, 4096)
+    cl = ClusterDecoder(P.row_ptr, P.col_idx, P.p, 25, -0.5, 3.0, 4096, 512)
+    syn = torch.from_numpy(pack_bits(sig).view(np.int64)).cuda()
+    cor = torch.zeros((60, cl.correction_words), dtype=torch.int64, device="cuda")
+    st, steps = cl.decode(syn, cor)
+    torch.cuda.synchronize()
+    cl.close()
+    cor = unpack_bits(cor.cpu().numpy().view(np.uint64), N)
+    st, steps = st.cpu().numpy(), steps.cpu().numpy()
+    L = bp_llrs(P.row_ptr, P.col_idx, P.p, sig, 25, precision="f32")
+    for b in range(60):
+        f, s_, n = bp_uf(H, sig[b], L[b], cp)
+        assert st[b] == s_ and steps[b] == n, (b, st[b], s_, steps[b], n)
+        if s_ == 1:
+            assert (cor[b] == f).all()

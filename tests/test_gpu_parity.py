@@ -145,6 +145,60 @@ def test_irregular_graph_with_degree_one_checks_and_erasures():
         assert_same_decisions(got, ref, f"irregular/{PREC[prec]}")
 
 
+def _random_graph(rng, M, N, dv_max, n_wide, dc_wide):
+    """Random H with fault degrees 1..dv_max, plus n_wide checks of degree in dc_wide."""
+    H = np.zeros((M, N), dtype=np.uint8)
+    for j in range(N):
+        H[rng.choice(M, int(rng.integers(1, dv_max + 1)), replace=False), j] = 1
+    for i in rng.choice(M, n_wide, replace=False):
+        H[i, :] = 0
+        free = np.nonzero(H.sum(0) < dv_max)[0]
+        H[i, rng.choice(free, int(rng.integers(*dc_wide)), replace=False)] = 1
+    return H
+
+
+def test_widest_check_family():
+    """Checks of degree 17..32 (the widest compiled family), both precisions."""
+    rng = np.random.default_rng(21)
+    from workloads import DecodingProblem
+    H = _random_graph(rng, 150, 300, 4, 6, (17, 33))
+    assert 16 < H.sum(1).max() <= 32 and H.sum(0).max() <= 8
+    p = rng.uniform(0.01, 0.1, 300)
+    P = DecodingProblem("wide", H, np.zeros((1, 300), np.uint8), p, {"code": "bb72"})
+    F = (rng.random((200, 300)) < p).astype(np.uint8)
+    sig = syndrome(P, F)
+    gam = gamma_for(P, R=20, seed=5)
+    for prec in (QLDPC_MSG_FP32, QLDPC_MSG_FP16):
+        cfg = RelayConfig(legs_after_first=20, stop_after_solutions=3, msg_precision=prec)
+        got = gpu_decode(P, gam, sig, cfg)
+        assert got[4].max_check_degree > 16
+        ref = relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig, _params(cfg),
+                           precision=PREC[prec])
+        assert_same_decisions(got, ref, f"wide/{PREC[prec]}")
+
+
+@pytest.mark.parametrize("prec", [QLDPC_MSG_FP32, QLDPC_MSG_FP16])
+def test_largest_graph_the_default_family_holds(prec):
+    """N = 12,000 faults: the largest shape of the degree-8/4 family (512 x 32); its
+    float32 message array (144 KB) and priors fill most of a block's shared memory."""
+    rng = np.random.default_rng(22)
+    from workloads import DecodingProblem
+    M, N = 4500, 12000
+    sockets = rng.permutation(np.repeat(np.arange(M), 8)).reshape(N, 3)  # 8 per check, 3 per fault
+    H = np.zeros((M, N), dtype=np.uint8)
+    H[sockets.ravel(), np.repeat(np.arange(N), 3)] = 1                 # repeated pairs merge
+    p = np.full(N, 0.002)
+    P = DecodingProblem("large", H, np.zeros((1, N), np.uint8), p, {"code": "bb72"})
+    F = (rng.random((40, N)) < p).astype(np.uint8)
+    sig = syndrome(P, F)
+    gam = gamma_for(P, R=10, seed=6)
+    cfg = RelayConfig(legs_after_first=10, stop_after_solutions=2, msg_precision=prec)
+    got = gpu_decode(P, gam, sig, cfg)
+    assert got[4].block_threads == 512 and got[4].max_check_degree <= 8
+    ref = relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig, _params(cfg), precision=PREC[prec])
+    assert_same_decisions(got, ref, "largest")
+
+
 def test_host_buffer_entry_point_matches_device_entry_point():
     P = problem("bb144_T12")
     F, sig = shots(P, 500, 6)
