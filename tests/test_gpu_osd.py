@@ -16,9 +16,6 @@ torch = pytest.importorskip("torch")
 from paper_2511_21660_gb300 import (FilteredOSD, QLDPC_OSD_SKIPPED, QLDPC_OSD_SOLVED,  # noqa: E402
                                     RelayConfig, RelayDecoder, first_leg_then_osd)
 
-STATUS = {1: QLDPC_OSD_SOLVED, -1: -1, -2: -2}
-
-
 def _shots(P, n, seed):
     F = sample_faults(P.p, seed, n)
     return F, syndromes_of(P.row_ptr, P.col_idx, F)
