@@ -137,3 +137,35 @@ def test_product_path_has_no_cpu_fallback():
             if f.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"(import|from)\s+oracle|oracle/|liboracle", src), f
+
+
+def test_post_processor_and_grouped_entry_points_reject_bad_input(lib):
+    from paper_2511_21660_gb300 import qldpc
+    rp = np.ascontiguousarray([0, 2, 4], dtype=np.int32)
+    ci = np.ascontiguousarray([0, 1, 1, 2], dtype=np.int32)
+    pr = np.ascontiguousarray([0.1, 0.1, 0.1])
+    h = ctypes.c_void_p()
+    for bp, conf, rmax in ((-1, 4.0, 500), (25, float("nan"), 500), (25, 4.0, 0),
+                           (25, 4.0, 1025)):
+        prm = qldpc.qldpc_osd_params(bp, conf, rmax)
+        rc = lib.qldpc_osd_create(ctypes.byref(h), 2, 3, rp.ctypes.data, ci.ctypes.data,
+                                  pr.ctypes.data, ctypes.byref(prm), 0)
+        assert rc == qldpc.QLDPC_ERR_INVALID_ARG and not h.value, (bp, conf, rmax)
+    for bp, acc, era, nc, nf in ((-1, -1.0, 1.0, 10, 10), (25, 1.0, -1.0, 10, 10),
+                                 (25, -1.0, float("inf"), 10, 10), (25, -1.0, 1.0, 0, 10),
+                                 (25, -1.0, 1.0, 4097, 10), (25, -1.0, 1.0, 10, 0),
+                                 (25, -1.0, 1.0, 10, 513)):
+        prm = qldpc.qldpc_cluster_params(bp, acc, era, nc, nf)
+        rc = lib.qldpc_cluster_create(ctypes.byref(h), 2, 3, rp.ctypes.data, ci.ctypes.data,
+                                      pr.ctypes.data, ctypes.byref(prm), 0)
+        assert rc == qldpc.QLDPC_ERR_INVALID_ARG and not h.value, (bp, acc, era, nc, nf)
+    assert lib.qldpc_osd_decode_batch(None, None, 1, None, None, None, None, None) == \
+        qldpc.QLDPC_ERR_INVALID_ARG
+    assert lib.qldpc_cluster_decode_batch(None, None, 1, None, None, None, None, None) == \
+        qldpc.QLDPC_ERR_INVALID_ARG
+    assert lib.qldpc_decode_batch_grouped(None, 0, None, None, 1, 1, None, 1, None, None,
+                                          None, None, 0, None) == qldpc.QLDPC_ERR_INVALID_ARG
+    assert qldpc.qldpc_grouped_workspace_bytes(3, 100) == 256 + 4 * 3 * 100
+    assert qldpc.qldpc_grouped_workspace_bytes(0, 100) == 0
+    lib.qldpc_osd_destroy(None)
+    lib.qldpc_cluster_destroy(None)
