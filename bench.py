@@ -687,16 +687,23 @@ def run_ours(args):
     alg_ops = ops_per_edge_iter * P.E * total_iters
     achieved = alg_ops / (ms / 1e3) / 1e12
     sms = dec.info.num_sms
-    peak = 128 * sms * 2070e6 / 1e12     # 128 lanes/clk/SM (4 schedulers x 32) at 2070 MHz
+    # 128 lanes/clk/SM (4 schedulers x 32) at the maximum SM clock measured on this machine
+    # (MEASURED_PEAKS.json), else the nominal 2070 MHz
+    mhz = 2070.0
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    peak = 128 * sms * mhz * 1e6 / 1e12
     smem_bytes = 4 * 4 * P.E * total_iters   # read nu, write mu, read mu, write nu (float32)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": traffic_per_launch(args),
-                "peak_kind": "derived: 128 lanes/clk/SM x %d SMs x 2070 MHz" % sms,
+                "peak_kind": "derived: 128 lanes/clk/SM x %d SMs x %.0f MHz (max SM clock)" % (sms, mhz),
                 "algorithmic": f"{ops_per_edge_iter} ops x E={P.E} x {total_iters} iterations "
                                f"= {alg_ops / 1e9:.1f} G ops per launch",
                 "smem_message_bytes_per_launch": smem_bytes,
                 "smem_GBps": smem_bytes / (ms / 1e3) / 1e9,
-                "smem_peak_GBps": 128 * sms * 2070e6 / 1e9,
+                "smem_peak_GBps": 128 * sms * mhz * 1e6 / 1e9,
                 # executed-instruction view from the same ncu summary: the fraction of
                 # issue slots used (the kernel is issue-bound; null if the summary is stale)
                 "issue_slots_used_frac": (lambda v: v / 100.0 if v is not None else None)(
