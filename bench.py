@@ -344,7 +344,7 @@ def timed_post(post, syn, base_cor, skip, stream, flush, steps=3, warmup=3):
     return sum(times) / len(times), cor, status, extra
 
 
-def post_processing_variants(args, dev, stream, flush):
+def post_processing_variants(args, dev, stream, flush, block_threads=0):
     """First Relay leg + filtered-OSD (paper Sec. 5) and first Relay leg + BP + cluster
     decoding (Sec. 2.5, Sec. 6), the paper's two post-processed decoders (Sec. 7.1),
     against full Relay on the gross 12-round model at p = 0.02, where the first leg
@@ -364,9 +364,11 @@ def post_processing_variants(args, dev, stream, flush):
     syn = pack_bits_t(syndromes_t(P.H, F))
     gam = gamma_table(P.N, 300, 0.125, -0.24, 0.66, 2)
     first = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam[:1],
-                         RelayConfig(legs_after_first=0, stop_after_solutions=1), device=dev.index)
+                         RelayConfig(legs_after_first=0, stop_after_solutions=1,
+                                     block_threads=block_threads), device=dev.index)
     relay = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam,
-                         RelayConfig(stop_after_solutions=S_SOLUTIONS), device=dev.index)
+                         RelayConfig(stop_after_solutions=S_SOLUTIONS,
+                                     block_threads=block_threads), device=dev.index)
     osd = FilteredOSD(P.row_ptr, P.col_idx, P.p, 25, conf, rmax, device=dev.index)
     accept, erase = -0.5, 4.5
     cluster = ClusterDecoder(P.row_ptr, P.col_idx, P.p, 25, accept, erase, 4096, 512,
@@ -759,7 +761,9 @@ def run_ours(args):
            "d2h_bytes_per_step": int(SHOTS * (cw * 8 + 4 + 1 + 4))}
     assert np.array_equal(h_cor.numpy(), out[0].cpu().numpy()), "host path differs"
 
-    variants["first_leg_then_post_processing"] = post_processing_variants(args, dev, stream, flush)
+    # the gross code's autotuned block size serves the p = 0.02 decodes too
+    variants["first_leg_then_post_processing"] = post_processing_variants(
+        args, dev, stream, flush, block_threads=dec.info.block_threads)
     variants["mixed_batch"] = mixed_batch_variant(args, dev, stream, flush)
     variants["soft_dmem_training_step"] = soft_dmem_variant(args, dev, stream, flush)
     cpu = cpu_oracle_rate(P, sig, gam) if args.cpu_baseline else None
