@@ -651,7 +651,7 @@ def run_ours(args):
     from paper_2511_21660_gb300.autotune import tune_block_threads
     cfg = RelayConfig(stop_after_solutions=S_SOLUTIONS, msg_precision=QLDPC_MSG_FP32,
                       kernel=QLDPC_KERNEL_FUSED)
-    bt, tuning = tune_block_threads(P.row_ptr, P.col_idx, P.p, gam, cfg, syn[:20000], cache=None)
+    bt, tuning = tune_block_threads(P.row_ptr, P.col_idx, P.p, gam, cfg, syn[:50000], cache=None)
     cfg.block_threads = bt
     dec = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam, cfg, device=local)
     out = dec.outputs(SHOTS)
@@ -716,7 +716,7 @@ def run_ours(args):
     cfg16 = RelayConfig(stop_after_solutions=S_SOLUTIONS, msg_precision=QLDPC_MSG_FP16,
                         kernel=QLDPC_KERNEL_FUSED)
     cfg16.block_threads, tuning16 = tune_block_threads(P.row_ptr, P.col_idx, P.p, gam, cfg16,
-                                                       syn[:20000], cache=None)
+                                                       syn[:50000], cache=None)
     for name, vcfg in (("fused_fp16", cfg16),
                        ("baseline_fp32", RelayConfig(stop_after_solutions=S_SOLUTIONS,
                                                      msg_precision=QLDPC_MSG_FP32,
@@ -778,7 +778,7 @@ def run_ours(args):
                    "messages": "float32", "kernel": "fused persistent",
                    "block_threads": dec.info.block_threads,
                    "blocks_per_sm": dec.info.blocks_per_sm, "grid": dec.info.grid_blocks,
-                   "autotune_ms_20k_shots": {str(k): round(v, 3) for k, v in tuning.items()},
+                   "autotune_ms_50k_shots": {str(k): round(v, 3) for k, v in tuning.items()},
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed between steps (256 MB write)"},
         "edge_updates_per_s": ws * P.E * total_iters / (ms / 1e3),

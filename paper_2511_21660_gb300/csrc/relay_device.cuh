@@ -37,6 +37,15 @@ struct Msg<__half> {
 
 __device__ __forceinline__ float clampc(float x, float c) { return fminf(fmaxf(x, -c), c); }
 
+// Binary16 store with saturation at the largest finite value, 65504: for every finite x
+// it equals rounding min(max(x, -65504), 65504) to nearest, i.e. the clamp to C = 65504
+// followed by the store.
+__device__ __forceinline__ void st_half_sat(unsigned char *base, int off, float v) {
+    unsigned short h;
+    asm("cvt.rn.satfinite.f16.f32 %0, %1;" : "=h"(h) : "f"(v));
+    *reinterpret_cast<unsigned short *>(base + off) = h;
+}
+
 // x + 0 = x for x != 0 and -0 + 0 = +0.  Applied to lambda(0) and to
 // (1 - gamma) lambda(0) at the start of a leg, it guarantees that lambda(t) and
 // therefore every stored message nu (a sum starting from lambda(t)) is never -0,
@@ -242,6 +251,25 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, con
 template <typename MT, int DV>
 __device__ __forceinline__ float fault_update(unsigned char *msg, const int (&sl)[DV], int deg,
                                               float lam, float C) {
+    // binary16 storage with C = 65504 (its default): the saturating store clamps the
+    // messages, so only the marginal needs an explicit clamp
+    if constexpr (sizeof(MT) == 2) {
+        if (C == 65504.0f && (deg == 3 || deg == 2)) {
+            const float mu0 = Msg<MT>::ld(msg, sl[0]), mu1 = Msg<MT>::ld(msg, sl[1]);
+            const float s0 = __fadd_rn(lam, mu0);
+            if (deg == 3) {
+                const float mu2 = Msg<MT>::ld(msg, sl[2]);
+                const float s01 = __fadd_rn(s0, mu1);
+                st_half_sat(msg, sl[0], __fadd_rn(__fadd_rn(lam, mu1), mu2));
+                st_half_sat(msg, sl[1], __fadd_rn(s0, mu2));
+                st_half_sat(msg, sl[2], s01);
+                return clampc(__fadd_rn(s01, mu2), C);
+            }
+            st_half_sat(msg, sl[0], __fadd_rn(lam, mu1));
+            st_half_sat(msg, sl[1], s0);
+            return clampc(__fadd_rn(s0, mu1), C);
+        }
+    }
     // The clamp is the identity unless some value exceeds C in magnitude, so it is
     // applied only then (same values either way).
     if (deg == 3) {

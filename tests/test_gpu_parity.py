@@ -199,6 +199,21 @@ def test_largest_graph_the_default_family_holds(prec):
     assert_same_decisions(got, ref, "largest")
 
 
+@pytest.mark.parametrize("prec", [QLDPC_MSG_FP32, QLDPC_MSG_FP16])
+def test_small_saturation_bound_clamps_like_the_oracle(prec):
+    """llr_clip = 12: messages and marginals saturate all the time (R11); both precisions
+    take the general clamp path (binary16's saturating store applies only at 65504)."""
+    P = problem("bb72_T6")
+    F, sig = shots(P, 400, 9)
+    gam = gamma_for(P, seed=9)
+    cfg = RelayConfig(stop_after_solutions=5, msg_precision=prec, llr_clip=12.0)
+    got = gpu_decode(P, gam, sig, cfg)
+    prm = _params(cfg)
+    prm.clip = 12.0
+    ref = relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig, prm, precision=PREC[prec])
+    assert_same_decisions(got, ref, f"clip12/{PREC[prec]}")
+
+
 def test_host_buffer_entry_point_matches_device_entry_point():
     P = problem("bb144_T12")
     F, sig = shots(P, 500, 6)
