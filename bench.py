@@ -219,11 +219,15 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
+KERNEL_SOURCES = ("relay_device.cuh", "relay_fused.cu", "qldpc_internal.h", "qldpc_api.cu")
+
+
 def kernel_source_sha1() -> str:
-    """sha1 (12 hex digits) of the fused decode kernel's sources, in include order."""
+    """sha1 (12 hex digits) of the fused decode kernel's sources and of the host code that
+    lays out its graph (edge placement, shared-memory layout), in that order."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("relay_device.cuh", "relay_fused.cu"):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2511_21660_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -250,8 +254,8 @@ def traffic_per_launch(args):
     dram__bytes_write.sum for a 20,000-shot launch of the same kernel; DRAM traffic
     (syndromes in, corrections out, graph and gamma rows) grows with the shot count,
     so it is scaled to the benchmark's shots.  None when the summary is absent or
-    was taken on a different kernel source (the sha1 of relay_device.cuh followed by
-    relay_fused.cu is recorded in the summary).
+    was taken on a different kernel source (the sha1 of KERNEL_SOURCES is recorded in the
+    summary).
     """
     path = os.path.join(ROOT, "profiles", "fused_decode_gross_T12.md")
     if not os.path.exists(path):

@@ -151,6 +151,70 @@ int pick_family(int dc, int dv, int fp16, const FusedKernel **tab, int *n) {
     return QLDPC_OK;
 }
 
+// Places each check's edges on the check's real slots (padding keeps its slots) so that
+// the fault pass's warp-wide accesses spread over the 32 shared-memory banks.  A warp
+// takes 32 consecutive faults and accesses, for each k, the message of each fault's
+// k-th edge: that is one access group, whose cost is its most crowded bank (the
+// wavefronts it takes), with the sum of squared bank counts as the tie-breaker.  The
+// check rule does not depend on where an edge sits in its check, so every placement
+// gives the same messages.  Local search: swap two edges of one check when that
+// lowers the cost (equal-cost swaps are taken now and then, from a fixed LCG stream,
+// to leave plateaus); at most 8 sweeps.  bank(i, k) = bank of logical slot k of check i;
+// pos[e] = the logical slot of edge e.
+template <typename BankFn>
+void place_edges(int M, int N, int DV, const int32_t *row_ptr, const int32_t *col_idx,
+                 BankFn bank, std::vector<int> &pos) {
+    const int E = row_ptr[M];
+    std::vector<int> cnt(N, 0), grp(E);
+    const size_t G = (size_t)(N + 31) / 32 * DV;
+    std::vector<int> hist(G * 32, 0);
+    pos.resize(E);
+    for (int i = 0; i < M; ++i)
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int j = col_idx[e];
+            pos[e] = e - row_ptr[i];
+            grp[e] = (j >> 5) * DV + cnt[j]++;  // rows ascending => the fault's k-th edge
+            ++hist[(size_t)grp[e] * 32 + bank(i, pos[e])];
+        }
+    auto cost = [&](int g) {
+        const int *h = &hist[(size_t)g * 32];
+        int mx = 0, sq = 0;
+        for (int b = 0; b < 32; ++b) {
+            mx = std::max(mx, h[b]);
+            sq += h[b] * h[b];
+        }
+        return mx * 65536 + sq;
+    };
+    auto move = [&](int g, int from, int to) {
+        --hist[(size_t)g * 32 + from];
+        ++hist[(size_t)g * 32 + to];
+    };
+    uint32_t lcg = 12345u;
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        int improved = 0;
+        for (int i = 0; i < M; ++i)
+            for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a)
+                for (int b = a + 1; b < row_ptr[i + 1]; ++b) {
+                    const int ga = grp[a], gb = grp[b];
+                    const int ba = bank(i, pos[a]), bb = bank(i, pos[b]);
+                    if (ba == bb) continue;
+                    const int before = cost(ga) + (gb != ga ? cost(gb) : 0);
+                    move(ga, ba, bb);
+                    move(gb, bb, ba);
+                    const int after = cost(ga) + (gb != ga ? cost(gb) : 0);
+                    lcg = lcg * 1664525u + 1013904223u;
+                    if (after < before || (after == before && (lcg >> 30) == 0u)) {
+                        std::swap(pos[a], pos[b]);
+                        improved += after < before;
+                    } else {
+                        move(ga, bb, ba);
+                        move(gb, ba, bb);
+                    }
+                }
+        if (!improved) break;
+    }
+}
+
 int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx,
                 const std::vector<float> &w, const float *gamma, int block_threads) {
     const int M = d->M, N = d->N, E = d->E;
@@ -196,10 +260,13 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
     std::vector<int32_t> var_chk((size_t)N * DV, 0), var_slot((size_t)N * DV, 0);
     std::vector<int32_t> slot_edge((size_t)g.Mp * DC, -1);
     std::vector<uint32_t> pad_mask((size_t)(g.Mp / 2) * DC, 0);
+    std::vector<int> pos;
+    place_edges(M, N, DV, row_ptr, col_idx,
+                [&](int i, int k) { return (byte_off(i, k) >> 2) & 31; }, pos);
     for (int i = 0; i < M; ++i) {
         chk_deg[i] = (uint8_t)(row_ptr[i + 1] - row_ptr[i]);
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int k = e - row_ptr[i], j = col_idx[e];
+            const int k = pos[e], j = col_idx[e];
             const int off = byte_off(i, k);
             slot_edge[off / msg_size] = e;
             var_chk[(size_t)j * DV + var_deg[j]] = i;

@@ -17,8 +17,10 @@ struct DevParams {
 };
 
 // Tanner graph in the layouts of the fused kernel.
-//   The k-th edge of check i (edges of a check in increasing fault order) has its
-//   message at physical position p = k ^ swz(i) of the check's DC-slot row:
+//   The edges of check i sit on its logical slots k = 0..deg-1 (slots deg..DC-1 are
+//   padding); which edge takes which slot is chosen at create time to spread the fault
+//   pass's accesses over the shared-memory banks.  Logical slot k of check i is the
+//   physical position p = k ^ swz(i) of the check's DC-slot row:
 //     float32:  element i*DC + p                      (byte offset 4 * element)
 //     binary16: checks 2q, 2q+1 share the 32-bit words q*DC + p, low half for even
 //               i (byte offset 4 * word + 2 * (i & 1)), swizzled by swz(q)

@@ -189,6 +189,10 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, cons
 // Check pass, binary16 messages: checks 2q and 2q+1 share each 32-bit word (low
 // and high half), processed together with half2 arithmetic; min, max and sign
 // manipulation are exact in any format.  A per-pair mask keeps C in padding halves.
+// Lanes read and write their row's 16-byte chunks in the order k4 ^ cs: rows are
+// 8*DC bytes apart, and cs = (row / rows per 128-byte line) mod chunks per row makes
+// each 128-bit access of a warp touch every bank equally often (no bank conflict).
+// The rule is symmetric in the slots, so only the padding mask follows the order.
 template <int NT, int DC>
 __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, const uint32_t *sg,
                                            uint32_t *par_zero, float C) {
@@ -202,10 +206,11 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, con
         uint32_t sx = ((sb & 1u) << 15) | ((sb & 2u) << 30);
         const bool full = g.chk_deg[i] == DC && g.chk_deg[i + 1] == DC;
         uint4 *row = reinterpret_cast<uint4 *>(msg + (size_t)q * 2 * DC);
+        const int cs = (q / (DC >= 32 ? 1 : 32 / DC)) & (DC / 4 - 1);
         uint32_t v[DC];
 #pragma unroll
         for (int k4 = 0; k4 < DC / 4; ++k4) {
-            const uint4 t = row[k4];
+            const uint4 t = row[k4 ^ cs];
             v[4 * k4] = t.x;
             v[4 * k4 + 1] = t.y;
             v[4 * k4 + 2] = t.z;
@@ -233,7 +238,7 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, con
             const uint4 *pm4 = reinterpret_cast<const uint4 *>(g.pad_mask + (size_t)q * DC);
 #pragma unroll
             for (int k4 = 0; k4 < DC / 4; ++k4) {
-                const uint4 t = __ldg(pm4 + k4);
+                const uint4 t = __ldg(pm4 + (k4 ^ cs));
                 o[4 * k4] = (o[4 * k4] & ~t.x) | (c2 & t.x);
                 o[4 * k4 + 1] = (o[4 * k4 + 1] & ~t.y) | (c2 & t.y);
                 o[4 * k4 + 2] = (o[4 * k4 + 2] & ~t.z) | (c2 & t.z);
@@ -242,7 +247,7 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, con
         }
 #pragma unroll
         for (int k4 = 0; k4 < DC / 4; ++k4)
-            row[k4] = make_uint4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
+            row[k4 ^ cs] = make_uint4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
     }
 }
 
