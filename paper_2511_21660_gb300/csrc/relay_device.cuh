@@ -136,6 +136,9 @@ __device__ __forceinline__ void leg_init(const FusedGraph &g, const DevParams &p
 // Padding slots hold C, which is also the min over an empty set, and keep it.
 // The sign is (-1)^sigma_i times the product of all signs times sign(nu_k).
 // Slots are processed in physical order: the rule does not depend on the order.
+// Lanes read and write their row's 16-byte chunks in the order k4 ^ cs: rows are
+// 4*DC bytes apart, and cs = (row / rows per 128-byte line) mod chunks per row makes
+// each 128-bit access of a warp touch every bank equally often (no bank conflict).
 template <int NT, int DC>
 __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, const uint32_t *sg,
                                            uint32_t *par_zero, float C) {
@@ -144,10 +147,11 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, cons
         const int deg = g.chk_deg[i];
         uint32_t sx = sg[i >> 5] << (31 - (i & 31));
         float4 *row = reinterpret_cast<float4 *>(msg + (size_t)i * DC);
+        const int cs = (i / (DC >= 32 ? 1 : 32 / DC)) & (DC / 4 - 1);  // chunk order
         float v[DC];
 #pragma unroll
         for (int k4 = 0; k4 < DC / 4; ++k4) {
-            const float4 t = row[k4];
+            const float4 t = row[k4 ^ cs];
             v[4 * k4] = t.x;
             v[4 * k4 + 1] = t.y;
             v[4 * k4 + 2] = t.z;
@@ -162,37 +166,33 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, cons
             sx ^= __float_as_uint(v[k]);
         }
         sx &= 0x80000000u;
-        // magnitude of slot k: m2 if |nu_k| = m1 (the smallest), else m1; every other
-        // |nu_k| is >= m2, so on the bit patterns of these non-negative floats
-        // bits(mag) = bits(m1) + bits(m2) - min(bits(|nu_k|), bits(m2)), exactly.
-        const uint32_t b12 = __float_as_uint(m1) + __float_as_uint(m2);
-        const uint32_t b2 = __float_as_uint(m2);
+        // Slot k holds a smallest magnitude iff |nu_k| <= m1 (no |nu_k| is below m1);
+        // its excluded minimum is then m2 (= m1 on a tie), else m1.  Both candidates
+        // carry the sign of the whole product; one XOR takes the slot's own sign out.
+        const uint32_t s1 = __float_as_uint(m1) | sx, s2 = __float_as_uint(m2) | sx;
         float o[DC];
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
-            const uint32_t vb = __float_as_uint(v[k]);
-            const uint32_t mag = b12 - min(vb & 0x7fffffffu, b2);
-            o[k] = __uint_as_float(mag | ((sx ^ vb) & 0x80000000u));
+            const uint32_t c = fabsf(v[k]) <= m1 ? s2 : s1;
+            o[k] = __uint_as_float(c ^ (__float_as_uint(v[k]) & 0x80000000u));
         }
-        if (deg < DC) {
-            const int f = swz<DC>(i);
+        if (deg < DC) {  // v[k] is physical slot k ^ 4cs, logical slot k ^ 4cs ^ swz(i)
+            const int f = swz<DC>(i) ^ (cs << 2);
 #pragma unroll
             for (int k = 0; k < DC; ++k)
                 if ((k ^ f) >= deg) o[k] = C;
         }
 #pragma unroll
         for (int k4 = 0; k4 < DC / 4; ++k4)
-            row[k4] = make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
+            row[k4 ^ cs] = make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
     }
 }
 
 // Check pass, binary16 messages: checks 2q and 2q+1 share each 32-bit word (low
 // and high half), processed together with half2 arithmetic; min, max and sign
 // manipulation are exact in any format.  A per-pair mask keeps C in padding halves.
-// Lanes read and write their row's 16-byte chunks in the order k4 ^ cs: rows are
-// 8*DC bytes apart, and cs = (row / rows per 128-byte line) mod chunks per row makes
-// each 128-bit access of a warp touch every bank equally often (no bank conflict).
-// The rule is symmetric in the slots, so only the padding mask follows the order.
+// Row chunks are visited in the order k4 ^ cs as in the float32 pass (rows of check
+// pairs are 4*DC bytes apart too); only the padding mask follows the order.
 template <int NT, int DC>
 __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, const uint32_t *sg,
                                            uint32_t *par_zero, float C) {
@@ -227,12 +227,13 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, con
         sx &= 0x80008000u;
         const uint32_t u1 = *reinterpret_cast<const uint32_t *>(&m1);
         const uint32_t u2 = *reinterpret_cast<const uint32_t *>(&m2);
+        const uint32_t s1 = u1 | sx, s2 = u2 | sx;  // candidates with the product's sign
         uint32_t o[DC];
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
             const __half2 a = __habs2(*reinterpret_cast<const __half2 *>(&v[k]));
             const uint32_t eq = __hle2_mask(a, m1);
-            o[k] = ((u2 & eq) | (u1 & ~eq)) | ((sx ^ v[k]) & 0x80008000u);
+            o[k] = ((s2 & eq) | (s1 & ~eq)) ^ (v[k] & 0x80008000u);
         }
         if (!full) {
             const uint4 *pm4 = reinterpret_cast<const uint4 *>(g.pad_mask + (size_t)q * DC);
