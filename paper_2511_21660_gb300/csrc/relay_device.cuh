@@ -332,8 +332,9 @@ __device__ __forceinline__ float fault_update(unsigned char *msg, const int (&sl
 // bitmap fw, and the syndrome of the decision: every fault with F_j = 1 flips the
 // parity bits of its checks in par (zeroed by the preceding check pass).  Decisions
 // are sparse, so this costs a few atomics per shot instead of a pass over all edges.
+// Returns the thread's decided faults (bit r: fault threadIdx.x + r*NT has F_j = 1).
 template <typename MT, int NT, int VPT, int DV, bool SKIP = false>
-__device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *msg, uint32_t *fw,
+__device__ __forceinline__ uint32_t fault_pass(const FusedGraph &g, unsigned char *msg, uint32_t *fw,
                                            uint32_t *par, float (&Lam)[VPT],
                                            const float (&bb)[VPT], const float (&gg)[VPT],
                                            float C) {
@@ -361,6 +362,7 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *m
     }
     // Decided faults are few: flip their checks' parity after the loop, so that the
     // per-fault body carries no divergent branch and no live edge state.
+    const uint32_t decided = dmask;
     while (dmask) {
         const int r = __ffs(dmask) - 1;
         dmask &= dmask - 1u;
@@ -372,6 +374,7 @@ __device__ __forceinline__ void fault_pass(const FusedGraph &g, unsigned char *m
             atomicXor(par + (c >> 5), 1u << (c & 31));
         }
     }
+    return decided;
 }
 
 // H F = sigma ?  Each warp compares the parity words with the syndrome on its own
@@ -382,31 +385,16 @@ __device__ __forceinline__ bool warp_converged(const uint32_t *par, const uint32
     return !__any_sync(FULL, bad != 0u);
 }
 
-// This thread's share of the solution weight sum_j F_j w_j (2^-33 units), reduced
-// over the warp; lane 0 stores the warp's partial in part[warp].  After a barrier
-// every thread adds the NT/32 partials: integer addition makes the total exact and
+// Adds this thread's share of the solution weight sum_j F_j w_j (2^-33 units) to the
+// block's accumulator: only the few threads with decided faults (mask dm from the
+// fault pass) issue an atomic.  Integer addition makes the total exact and
 // independent of the order.
-template <int NT, int VPT, bool SKIP = false>
-__device__ __forceinline__ void warp_weight(const FusedGraph &g, const float *ws,
-                                            const float (&Lam)[VPT], long long *part) {
-    long long s = 0;
-#pragma unroll
-    for (int r = 0; r < VPT; ++r) {
-        if (SKIP && r * NT >= g.N) break;
-        const int j = threadIdx.x + r * NT;
-        if (j < g.N && Lam[r] < 0.0f) s += wfix(ws[j]);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-}
-
 template <int NT>
-__device__ __forceinline__ long long total_weight(const long long *part) {
-    long long W = 0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) W += part[w];
-    return W;
+__device__ __forceinline__ void add_weight(const float *ws, uint32_t dm, long long *acc) {
+    long long w = 0;
+    for (uint32_t m = dm; m; m &= m - 1u) w += wfix(ws[threadIdx.x + (__ffs(m) - 1) * NT]);
+    if (w != 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(acc), (unsigned long long)w);
 }
 
 template <int NT>

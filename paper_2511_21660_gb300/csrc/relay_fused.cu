@@ -35,18 +35,22 @@ namespace {
 
 // Relay on one shot: the leg schedule around the check and fault passes.  Per
 // iteration: check pass | barrier | fault pass | barrier | per-warp convergence
-// test.  A leg end adds the weight reduction, the next leg's initialisation and one
+// test.  A leg end adds the weight sum, the next leg's initialisation and one
 // barrier.  Called by every thread of the block with block-uniform arguments.
 // SKIP: the shot's code may use only part of the block's fault slots (mixed batches),
 // so the per-fault loops stop at the code's last slot.
+// wacc[2]: the block's weight accumulators, used in turn (ab selects the one the next
+// new solution adds into); the other one is zeroed after each use, at least two
+// barriers before it is added into again.  Both start at zero and ab persists across
+// the block's shots.
 template <typename MT, int NT, int VPT, int DC, int DV, bool SKIP = false>
 __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams &p, int shot,
                                             const uint64_t *sy, uint64_t *cor, DecodeOut out,
                                             unsigned char *msg, uint32_t *fw, uint32_t *fb,
                                             uint32_t *sg, uint32_t *par, float *ws,
-                                            long long *s_Wpart,
+                                            long long *wacc,
                                             float (&Lam)[VPT], float (&bb)[VPT],
-                                            float (&gg)[VPT]) {
+                                            float (&gg)[VPT], int &ab) {
     const int tid = threadIdx.x;
     const float C = p.clip;
     load_syndrome<NT>(g, sy, sg);
@@ -59,7 +63,7 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
         uint32_t *pc = par + pb * g.m_words;
         check_pass<NT, DC>(g, reinterpret_cast<MT *>(msg), sg, pc, C);
         __syncthreads();
-        fault_pass<MT, NT, VPT, DV, SKIP>(g, msg, fw, pc, Lam, bb, gg, C);
+        const uint32_t dm = fault_pass<MT, NT, VPT, DV, SKIP>(g, msg, fw, pc, Lam, bb, gg, C);
         __syncthreads();
         ++iters;
         ++t;
@@ -71,7 +75,7 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
         // a solution equal to the kept one has its weight and cannot replace it
         const bool fresh = conv && !(have && warp_same_solution(fw, fb, 2 * g.cor_words));
         if (conv) ++sols;
-        if (fresh) warp_weight<NT, VPT, SKIP>(g, ws, Lam, s_Wpart);
+        if (fresh) add_weight<NT>(ws, dm, wacc + ab);
         const bool done = sols >= p.S || leg == p.R || spent;
         if (!done) {
             ++leg;
@@ -80,12 +84,14 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
         }
         __syncthreads();  // the weight and the next leg's initial messages are visible
         if (fresh) {
-            const long long W = total_weight<NT>(s_Wpart);
+            const long long W = wacc[ab];
             if (!have || W < Wbest) {
                 keep_solution<NT>(cor, fw, fb, g.cor_words);
                 have = true;
                 Wbest = W;
             }
+            if (tid == 0) wacc[ab ^ 1] = 0;
+            ab ^= 1;
         }
         if (done) break;
     }
@@ -110,12 +116,14 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
     float *ws;
     smem_layout(g, smem_raw, fw, fb, sg, par, ws);
     __shared__ int s_shot;
-    __shared__ long long s_Wpart[NT / 32];
+    __shared__ long long s_wacc[2];
     block_setup<MT, NT, DC>(g, msg, fw, ws, p.clip);
 
     float Lam[VPT], bb[VPT], gg[VPT];
 #pragma unroll
     for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
+    int ab = 0;
+    if (threadIdx.x < 2) s_wacc[threadIdx.x] = 0;
 
     const int limit = map.order ? min(*map.count, B) : B;
     for (;;) {
@@ -129,7 +137,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
         if (shot < 0) break;
         decode_shot<MT, NT, VPT, DC, DV>(g, p, shot, syn + (size_t)shot * map.syn_stride,
                                          out.corr + (size_t)shot * map.cor_stride, out, msg, fw,
-                                         fb, sg, par, ws, s_Wpart, Lam, bb, gg);
+                                         fb, sg, par, ws, s_wacc, Lam, bb, gg, ab);
     }
 }
 
@@ -147,12 +155,14 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode_multi(MultiTable tab,
     __shared__ FusedGraph s_g;
     __shared__ DevParams s_p;
     __shared__ int s_shot, s_code;
-    __shared__ long long s_Wpart[NT / 32];
+    __shared__ long long s_wacc[2];
     int cur = -1;
 
     float Lam[VPT], bb[VPT], gg[VPT];
 #pragma unroll
     for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
+    int ab = 0;
+    if (threadIdx.x < 2) s_wacc[threadIdx.x] = 0;
 
     for (;;) {
         __syncthreads();
@@ -188,7 +198,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode_multi(MultiTable tab,
         }
         decode_shot<MT, NT, VPT, DC, DV, true>(s_g, s_p, shot, syn + (size_t)shot * syn_stride,
                                          out.corr + (size_t)shot * cor_stride, out, msg, fw, fb,
-                                         sg, par, ws, s_Wpart, Lam, bb, gg);
+                                         sg, par, ws, s_wacc, Lam, bb, gg, ab);
     }
 }
 
