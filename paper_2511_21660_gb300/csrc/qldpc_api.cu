@@ -239,7 +239,7 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
     g.Mp = (M + 31) / 32 * 32;
     g.syn_words = (M + 63) / 64;
     g.cor_words = (N + 63) / 64;
-    g.f_words = 2 * g.cor_words + 2;
+    g.f_words = (2 * g.cor_words + 2 + 3) & ~3;  // whole 16-byte groups
     g.m_words = (M + 31) / 32;
 
     // message layout (see FusedGraph): rows of DC slots, swizzled inside a row

@@ -30,7 +30,8 @@ struct FusedGraph {
     int msg_bytes;        // bytes of the message array (Mp * DC * message size)
     int syn_words;        // ceil(M/64) uint64 words per syndrome
     int cor_words;        // ceil(N/64) uint64 words per correction
-    int f_words;          // uint32 words of the decision bitmap (2*cor_words + 2)
+    int f_words;          // uint32 words of the decision bitmap (2*cor_words + 2, rounded
+                          // up to a multiple of 4)
     int m_words;          // ceil(M/32) uint32 words of a parity bitmap
     const uint8_t *chk_deg;   // [Mp] check degrees (0 for rows M..Mp-1)
     const int32_t *var_chk;   // [N][DV] checks of fault j, increasing order
