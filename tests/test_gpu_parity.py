@@ -228,6 +228,23 @@ def test_host_buffer_entry_point_matches_device_entry_point():
     assert (legs == dev[1]).all() and (conv == dev[2]).all() and (iters == dev[3]).all()
 
 
+@pytest.mark.parametrize("name", ["bb72_cc", "bb144_T12"])
+def test_host_buffer_entry_point_matches_device_entry_point_on_a_large_batch(name):
+    """A batch of 16 grids of shots and a ragged remainder through the host buffers."""
+    P = problem(name)
+    gam = gamma_for(P, seed=7)
+    cfg = RelayConfig(stop_after_solutions=5)
+    dec = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam, cfg)
+    n = 16 * dec.info.grid_blocks + 37
+    F, sig = shots(P, n, 7)
+    cor, legs, conv, iters = dec.decode_host(pack_bits(sig))
+    dec.close()
+    dev = gpu_decode(P, gam, sig, cfg)
+    from workloads import unpack_bits
+    assert (unpack_bits(cor, P.N) == dev[0]).all()
+    assert (legs == dev[1]).all() and (conv == dev[2]).all() and (iters == dev[3]).all()
+
+
 @pytest.mark.parametrize("prec", [QLDPC_MSG_FP32, QLDPC_MSG_FP16])
 def test_first_iterations_match_fp64_oracle(prec):
     """Messages and marginals over the first 10 iterations (relative error in LLR units)."""
