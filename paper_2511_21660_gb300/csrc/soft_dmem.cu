@@ -26,10 +26,20 @@ constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
 struct RM;
+// float32: tanh(x/2) and atanh from the hardware exponential and logarithm and an
+// approximate division (absolute errors of a few 1e-7, far inside the float32 path's
+// tolerance against the FP64 oracle); FP64 keeps the library functions.
 template <>
 struct RM<float> {
-    static __device__ __forceinline__ float tanh_(float x) { return tanhf(x); }
-    static __device__ __forceinline__ float atanh_(float x) { return atanhf(x); }
+    // tanh(x/2) = 1 - 2/(1 + e^x); e^x = inf gives 1 and e^x = 0 gives -1
+    static __device__ __forceinline__ float tanh_half(float x) {
+        return 1.0f - __fdividef(2.0f, 1.0f + __expf(x));
+    }
+    // atanh(x) = log((1 + x)/(1 - x)) / 2, for |x| <= 1 - 2^-23 (products are clamped)
+    static __device__ __forceinline__ float atanh_(float x) {
+        return 0.5f * __logf(__fdividef(1.0f + x, 1.0f - x));
+    }
+    static __device__ __forceinline__ float div(float x, float y) { return __fdividef(x, y); }
     static __device__ __forceinline__ float softplus(float x) {
         return x > 0.0f ? x + log1pf(expf(-x)) : log1pf(expf(x));
     }
@@ -39,8 +49,9 @@ struct RM<float> {
 };
 template <>
 struct RM<double> {
-    static __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
+    static __device__ __forceinline__ double tanh_half(double x) { return tanh(x / 2.0); }
     static __device__ __forceinline__ double atanh_(double x) { return atanh(x); }
+    static __device__ __forceinline__ double div(double x, double y) { return x / y; }
     static __device__ __forceinline__ double softplus(double x) {
         return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x));
     }
@@ -84,18 +95,31 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
 }
 
 // Check products of one row: P_k = prod_{l != k} tanh(nu_l/2), clamped.  The row
-// has d <= DCM edges.
+// has d <= DCM edges.  float32 forms them from prefix and suffix products (O(d));
+// FP64 multiplies in increasing l, as the oracle does.
 template <typename T, int DCM>
 __device__ __forceinline__ void row_products(const T *nu_row, int d, T eps, T (&tau)[DCM],
                                              T (&P)[DCM], bool (&cl)[DCM]) {
 #pragma unroll
-    for (int k = 0; k < DCM; ++k) tau[k] = k < d ? RM<T>::tanh_(nu_row[k] / T(2)) : T(1);
+    for (int k = 0; k < DCM; ++k) tau[k] = k < d ? RM<T>::tanh_half(nu_row[k]) : T(1);
+    T suf[DCM];
+    if constexpr (sizeof(T) == 4) {
+        suf[DCM - 1] = T(1);
+#pragma unroll
+        for (int k = DCM - 2; k >= 0; --k) suf[k] = suf[k + 1] * tau[k + 1];
+    }
+    T pre = T(1);
 #pragma unroll
     for (int k = 0; k < DCM; ++k) {
         T prod = T(1);
+        if constexpr (sizeof(T) == 4) {
+            prod = pre * suf[k];
+            pre *= tau[k];
+        } else {
 #pragma unroll
-        for (int l = 0; l < DCM; ++l)
-            if (l != k && l < d) prod *= tau[l];
+            for (int l = 0; l < DCM; ++l)
+                if (l != k && l < d) prod *= tau[l];
+        }
         cl[k] = false;
         if (prod > T(1) - eps) {
             prod = T(1) - eps;
@@ -129,6 +153,24 @@ __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint6
     for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
         const int b = g.var_ptr[j], d = g.var_ptr[j + 1] - b;
         const T lam = (T(1) - a.gamma[j]) * a.w[j] + a.gamma[j] * Lam[j];
+        // degrees 3 and 2 in registers, with the generic loop's order of additions
+        if (d == 3 || d == 2) {
+            const int e0 = g.var_edges[b], e1 = g.var_edges[b + 1];
+            const T m0 = nu[e0], m1 = nu[e1];
+            if (d == 3) {
+                const int e2 = g.var_edges[b + 2];
+                const T m2 = nu[e2];
+                Lam[j] = lam + m0 + m1 + m2;
+                nu[e0] = lam + m1 + m2;
+                nu[e1] = lam + m0 + m2;
+                nu[e2] = lam + m0 + m1;
+            } else {
+                Lam[j] = lam + m0 + m1;
+                nu[e0] = lam + m1;
+                nu[e1] = lam + m0;
+            }
+            continue;
+        }
         T mu[8];
         for (int k = 0; k < d; ++k) mu[k] = nu[g.var_edges[b + k]];
         T L = lam;
@@ -223,18 +265,34 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
         }
         __syncthreads();
         for (int t = t1; t > t0; --t) {
-            const T *nu_prev = segb + (size_t)(t - t0 - 1) * EN;
-            const T *L_prev = nu_prev + g.E;
+            // the state before iteration t, staged in the forward arrays (free here)
+            copy_state(segb + (size_t)(t - t0 - 1) * EN, segb + (size_t)(t - t0 - 1) * EN + g.E,
+                       nu, g.E, g.N);
+            __syncthreads();
+            const T *nu_prev = nu;
+            const T *L_prev = Lam;
             const bool inner = t - 1 >= 1;
             // fault adjoint: lambda_bar = Lb + sum nb;  mu_bar_e = lambda_bar - nb_e
             for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
                 const int e0 = g.var_ptr[j], d = g.var_ptr[j + 1] - e0;
-                T sum = 0;
-                for (int k = 0; k < d; ++k) sum += nb[g.var_edges[e0 + k]];
-                const T lb = Lb[j] + sum;
-                for (int k = 0; k < d; ++k) {
-                    const int e = g.var_edges[e0 + k];
-                    nb[e] = lb - nb[e];
+                T lb;
+                if (d == 3 || d == 2) {  // in registers, same order of additions
+                    const int f0 = g.var_edges[e0], f1 = g.var_edges[e0 + 1];
+                    const int f2 = d == 3 ? g.var_edges[e0 + 2] : f1;
+                    const T n0 = nb[f0], n1 = nb[f1];
+                    const T n2 = d == 3 ? nb[f2] : T(0);
+                    lb = Lb[j] + (d == 3 ? T(0) + n0 + n1 + n2 : T(0) + n0 + n1);
+                    nb[f0] = lb - n0;
+                    nb[f1] = lb - n1;
+                    if (d == 3) nb[f2] = lb - n2;
+                } else {
+                    T sum = 0;
+                    for (int k = 0; k < d; ++k) sum += nb[g.var_edges[e0 + k]];
+                    lb = Lb[j] + sum;
+                    for (int k = 0; k < d; ++k) {
+                        const int e = g.var_edges[e0 + k];
+                        nb[e] = lb - nb[e];
+                    }
                 }
                 gs[j] += lb * (L_prev[j] - a.w[j]);
                 Lb[j] = inner ? lb * a.gamma[j] : T(0);
@@ -255,7 +313,7 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
                     if (k < d) {
                         const T mb = nb[e0 + k];
                         apart += mb * s2 * RM<T>::atanh_(P[k]);
-                        if (!cl[k]) Pb[k] = mb * at * s2 / (T(1) - P[k] * P[k]);
+                        if (!cl[k]) Pb[k] = RM<T>::div(mb * at * s2, T(1) - P[k] * P[k]);
                     }
                 }
                 // tau_bar_k = sum_{m != k} Pb_m prod_{l != m, k} tau_l in O(d), without
