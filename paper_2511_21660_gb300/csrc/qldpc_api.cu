@@ -849,13 +849,13 @@ struct qldpc_soft {
 
 namespace {
 
-size_t soft_workspace_layout(const qldpc_soft *s, int64_t B, size_t off[5]) {
+size_t soft_workspace_layout(const qldpc_soft *s, int64_t B, size_t off[6]) {
     const size_t rs = s->fp64 ? 8 : 4, EN = (size_t)s->E + s->N;
     const int nck = (s->T + s->K - 1) / s->K;
-    const size_t sz[5] = {(size_t)B * nck * EN * rs, (size_t)B * s->K * EN * rs, (size_t)B * rs,
-                          (size_t)B * s->N * rs, (size_t)B * s->T * rs};
+    const size_t sz[6] = {(size_t)B * nck * EN * rs, (size_t)B * s->K * EN * rs, (size_t)B * rs,
+                          (size_t)B * s->N * rs, (size_t)B * s->T * rs, (size_t)B * s->N * rs};
     size_t o = 0;
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < 6; ++q) {
         off[q] = o;
         o = align_up(o + sz[q], 256);
     }
@@ -864,7 +864,7 @@ size_t soft_workspace_layout(const qldpc_soft *s, int64_t B, size_t off[5]) {
 
 int soft_check_call(const qldpc_soft *s, const uint64_t *syn, const uint64_t *faults, int64_t B,
                     const void *gamma, const void *alpha, void *ws, uint64_t ws_bytes,
-                    size_t off[5]) {
+                    size_t off[6]) {
     if (!s) return fail(QLDPC_ERR_INVALID_ARG, "soft handle is NULL");
     if (B < 1 || B > 0x7fffffffLL) return fail(QLDPC_ERR_INVALID_ARG, "batch size out of range");
     if (!syn || !faults || !gamma || !alpha || !ws)
@@ -882,7 +882,7 @@ int soft_check_call(const qldpc_soft *s, const uint64_t *syn, const uint64_t *fa
 
 SoftLaunch soft_launch(const qldpc_soft *s, const uint64_t *syn, const uint64_t *faults,
                        int64_t B, const void *gamma, const void *alpha, void *ws,
-                       const size_t off[5]) {
+                       const size_t off[6]) {
     SoftLaunch L{};
     char *base = static_cast<char *>(ws);
     L.g = s->g;
@@ -902,6 +902,7 @@ SoftLaunch soft_launch(const qldpc_soft *s, const uint64_t *syn, const uint64_t 
     L.shot_loss = base + off[2];
     L.shot_gg = base + off[3];
     L.shot_ga = base + off[4];
+    L.shot_lb = base + off[5];
     return L;
 }
 
@@ -1005,7 +1006,7 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
 
 int qldpc_soft_workspace_bytes(const qldpc_soft *s, int64_t B, uint64_t *bytes) {
     if (!s || !bytes || B < 0) return fail(QLDPC_ERR_INVALID_ARG, "bad argument");
-    size_t off[5];
+    size_t off[6];
     *bytes = soft_workspace_layout(s, B, off);
     return QLDPC_OK;
 }
@@ -1014,7 +1015,7 @@ int qldpc_soft_forward(qldpc_soft *s, const uint64_t *syndromes, const uint64_t 
                        const void *gamma, const void *alpha, void *loss, void *marginals,
                        void *workspace, uint64_t workspace_bytes, void *stream) {
     g_last_error.clear();
-    size_t off[5];
+    size_t off[6];
     int rc = soft_check_call(s, syndromes, faults, B, gamma, alpha, workspace, workspace_bytes, off);
     if (rc) return rc;
     if (!loss || !is_device_ptr(loss)) return fail(QLDPC_ERR_INVALID_ARG, "loss must be device memory");
@@ -1034,7 +1035,7 @@ int qldpc_soft_backward(qldpc_soft *s, const uint64_t *syndromes, const uint64_t
                         void *grad_gamma, void *grad_alpha, void *workspace,
                         uint64_t workspace_bytes, void *stream) {
     g_last_error.clear();
-    size_t off[5];
+    size_t off[6];
     int rc = soft_check_call(s, syndromes, faults, B, gamma, alpha, workspace, workspace_bytes, off);
     if (rc) return rc;
     if (!grad_gamma || !grad_alpha || !is_device_ptr(grad_gamma) || !is_device_ptr(grad_alpha))

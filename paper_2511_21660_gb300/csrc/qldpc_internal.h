@@ -248,7 +248,7 @@ struct SoftLaunch {
     double eps;
     const uint64_t *syn, *faults;
     const void *gamma, *alpha, *w, *upstream;
-    void *ckpt, *seg, *shot_loss, *shot_gg, *shot_ga;
+    void *ckpt, *seg, *shot_loss, *shot_gg, *shot_ga, *shot_lb;
     void *loss, *marg, *grad_gamma, *grad_alpha;
 };
 

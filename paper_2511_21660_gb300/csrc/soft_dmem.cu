@@ -73,6 +73,7 @@ struct SoftArgs {
     T *shot_loss;  // [B]
     T *shot_gg;    // [B][N]
     T *shot_ga;    // [B][T]
+    T *shot_lb;    // [B][N] adjoint of Lambda (backward scratch)
     T *marg;       // [B][N] or nullptr
 };
 
@@ -226,9 +227,11 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_forward(SoftArgs<T> a) {
     if (threadIdx.x == 0) a.shot_loss[b] = tot;
 }
 
-// Adjoint.  Shared memory: nu[E], Lam[N] (forward recompute), nb[E] (adjoint of
-// nu(t), then of mu(t)), Lb[N] (adjoint of Lambda), gs[N] (gamma gradient of the
-// shot), as[T] (alpha gradient of the shot).
+// Adjoint.  Shared memory: nu[E], Lam[N] (forward recompute, then each reverse step's
+// saved state), nb[E] (adjoint of nu(t), then of mu(t)), as[T] (alpha gradient of the
+// shot).  The adjoint of Lambda and the gamma gradient of fault j are touched only by
+// the thread that owns j, so they stay in global memory (shot_lb, shot_gg: coalesced,
+// cached), which keeps the block's shared state small enough for 3 blocks per SM.
 template <typename T, int DCM>
 __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -236,11 +239,11 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
     T *nu = reinterpret_cast<T *>(smem_raw);
     T *Lam = nu + g.E;
     T *nb = Lam + g.N;
-    T *Lb = nb + g.E;
-    T *gs = Lb + g.N;
-    T *as = gs + g.N;
+    T *as = nb + g.E;
     __shared__ T red[SOFT_THREADS / 32];
     const int b = blockIdx.x;
+    T *Lb = a.shot_lb + (size_t)b * g.N;
+    T *gs = a.shot_gg + (size_t)b * g.N;
     const uint64_t *sy = a.syn + (size_t)b * g.syn_words;
     const uint64_t *fy = a.faults + (size_t)b * g.cor_words;
     const size_t EN = (size_t)g.E + g.N;
@@ -348,7 +351,6 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
         }
         __syncthreads();
     }
-    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) a.shot_gg[(size_t)b * g.N + j] = gs[j];
     for (int t = threadIdx.x; t < a.T_it; t += SOFT_THREADS) a.shot_ga[(size_t)b * a.T_it + t] = as[t];
 }
 
@@ -366,7 +368,7 @@ template <typename T>
 size_t fwd_smem(const SoftGraph &g) { return sizeof(T) * ((size_t)g.E + g.N); }
 template <typename T>
 size_t bwd_smem(const SoftGraph &g, int Tit) {
-    return sizeof(T) * (2 * ((size_t)g.E + g.N) + g.N + Tit);
+    return sizeof(T) * (2 * (size_t)g.E + g.N + Tit);
 }
 
 template <typename T, int DCM>
@@ -388,6 +390,7 @@ cudaError_t run_forward_t(const SoftLaunch &L, cudaStream_t st) {
     a.shot_loss = static_cast<T *>(L.shot_loss);
     a.shot_gg = static_cast<T *>(L.shot_gg);
     a.shot_ga = static_cast<T *>(L.shot_ga);
+    a.shot_lb = static_cast<T *>(L.shot_lb);
     a.marg = static_cast<T *>(L.marg);
     const size_t sm = fwd_smem<T>(L.g);
     cudaError_t e = cudaFuncSetAttribute(soft_forward<T, DCM>,
@@ -421,6 +424,7 @@ cudaError_t run_backward_t(const SoftLaunch &L, cudaStream_t st) {
     a.shot_loss = static_cast<T *>(L.shot_loss);
     a.shot_gg = static_cast<T *>(L.shot_gg);
     a.shot_ga = static_cast<T *>(L.shot_ga);
+    a.shot_lb = static_cast<T *>(L.shot_lb);
     const size_t sm = bwd_smem<T>(L.g, L.T_it);
     cudaError_t e = cudaFuncSetAttribute(soft_backward<T, DCM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
