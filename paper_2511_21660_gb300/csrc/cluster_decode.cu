@@ -110,8 +110,11 @@ __device__ __forceinline__ bool stream_cluster_rows(const FusedGraph &g, const C
     return true;
 }
 
+// Two blocks per SM where the kernel fits in 64 registers without spilling (8 faults
+// per thread, rows of up to 16 slots): the single-warp stages of one shot then overlap
+// the other block's work.
 template <int NT, int VPT, int DC, int DV>
-__global__ void __launch_bounds__(NT, 1) cluster_decode(FusedGraph g, DevParams p, ClusterArgs a,
+__global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_decode(FusedGraph g, DevParams p, ClusterArgs a,
                                                         const uint64_t *__restrict__ syn,
                                                         const uint8_t *__restrict__ skip, int B,
                                                         ClusterOut out, unsigned int *counter) {

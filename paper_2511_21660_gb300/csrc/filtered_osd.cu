@@ -52,8 +52,11 @@ __device__ __forceinline__ void bitonic_sort(uint64_t *keys, int n) {
     }
 }
 
+// Two blocks per SM where the kernel fits in 64 registers without spilling (8 faults
+// per thread, rows of up to 16 slots): the single-warp stages of one shot then overlap
+// the other block's work.
 template <int NT, int VPT, int DC, int DV>
-__global__ void __launch_bounds__(NT, 1) osd_decode(FusedGraph g, DevParams p, OsdArgs o,
+__global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) osd_decode(FusedGraph g, DevParams p, OsdArgs o,
                                                     const uint64_t *__restrict__ syn,
                                                     const uint8_t *__restrict__ skip, int B,
                                                     OsdOut out, unsigned int *counter) {
