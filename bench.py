@@ -575,16 +575,16 @@ def mixed_batch_variant(args, dev, stream, flush):
             "separate_total_ms": sum(v["ms"] for v in alone.values())}
 
 
-def soft_dmem_variant(args, dev, stream, flush):
+def soft_dmem_variant(args, dev, stream, flush, B=4096):
     """One training step of the differentiable leg: unrolled soft DMem-BP (25 iterations,
     trainable gamma_j and alpha_t, BCE loss, checkpoints every 5 iterations, float32) on
-    a batch of 4096 gross T=12 shots at p = 0.003: forward and adjoint times."""
+    a batch of B (4096) gross T=12 shots at p = 0.003: forward and adjoint times."""
     import torch
 
     from paper_2511_21660_gb300 import SoftDMem
     from workloads.torch_sampling import pack_bits_t, sample_faults_t, syndromes_t
     P = phenomenological_dem(BB144, 12, 0.003)
-    B, T = 4096, 25
+    T = 25
     F = sample_faults_t(P.p, 20, B, device=dev)
     syn = pack_bits_t(syndromes_t(P.H, F))
     faults = pack_bits_t(F)
@@ -607,7 +607,7 @@ def soft_dmem_variant(args, dev, stream, flush):
             fwd.append(e[0].elapsed_time(e[1]))
             bwd.append(e[1].elapsed_time(e[2]))
     f_ms, b_ms = sum(fwd) / len(fwd), sum(bwd) / len(bwd)
-    out = {"workload": "gross T=12 p=0.003, batch 4096, 25 iterations, checkpoint every 5, "
+    out = {"workload": f"gross T=12 p=0.003, batch {B}, 25 iterations, checkpoint every 5, "
                        "float32, gamma_j (2736) and alpha_t (25) trainable",
            "forward_ms": f_ms, "backward_ms": b_ms,
            "step_shots_per_s": B / ((f_ms + b_ms) / 1e3),
@@ -827,7 +827,30 @@ def main():
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--solutions", type=int, default=S_SOLUTIONS,
                     help="S of a decode-only run")
+    ap.add_argument("--only-post", action="store_true",
+                    help="profiling driver: the p = 0.02 first-leg, full-Relay, filtered-OSD and "
+                         "cluster-decoder comparison only")
+    ap.add_argument("--only-soft", type=int, default=0, metavar="B",
+                    help="profiling driver: one soft DMem-BP training-step measurement on a "
+                         "batch of B gross shots (no decode, e2e or CPU baseline)")
     args = ap.parse_args()
+    if args.only_soft:
+        import torch
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        args.cpu_baseline = False
+        r = soft_dmem_variant(args, dev, torch.cuda.Stream(dev), flush, B=args.only_soft)
+        print(json.dumps({"mode": "soft-only", **r}))
+        return
+    if args.only_post:
+        import torch
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        args.cpu_baseline = False
+        r = post_processing_variants(args, dev, torch.cuda.Stream(dev), flush,
+                                     block_threads=args.block_threads)
+        print(json.dumps({"mode": "post-only", **r}))
+        return
     if (args.shots != SHOTS or args.kernel != "fused" or args.msg != "fp32"
             or args.block_threads or args.solutions != S_SOLUTIONS):
         args.only_decode = True

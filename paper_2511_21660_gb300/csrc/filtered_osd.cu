@@ -52,11 +52,11 @@ __device__ __forceinline__ void bitonic_sort(uint64_t *keys, int n) {
     }
 }
 
-// Two blocks per SM where the kernel fits in 64 registers without spilling (8 faults
-// per thread, rows of up to 16 slots): the single-warp stages of one shot then overlap
-// the other block's work.
+// Several blocks per SM where the kernel fits in 64 registers without spilling (256
+// threads x 12 faults: 4 blocks; 512 x 8 with rows of up to 16 slots: 2): the single-warp
+// stages and barriers of one shot then overlap the other blocks' work.
 template <int NT, int VPT, int DC, int DV>
-__global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) osd_decode(FusedGraph g, DevParams p, OsdArgs o,
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 : 1)) osd_decode(FusedGraph g, DevParams p, OsdArgs o,
                                                     const uint64_t *__restrict__ syn,
                                                     const uint8_t *__restrict__ skip, int B,
                                                     OsdOut out, unsigned int *counter) {
@@ -230,7 +230,7 @@ OsdKernel osd_entry() {
 void osd_table(const OsdKernel **out, int *n) {
     // per (DC, DV) family of the fused layout: the first entry with threads * vpt >= N
     static const OsdKernel table[] = {
-        osd_entry<512, 8, 8, 4>(),  osd_entry<512, 16, 8, 4>(),
+        osd_entry<256, 12, 8, 4>(), osd_entry<512, 8, 8, 4>(),  osd_entry<512, 16, 8, 4>(),
         osd_entry<512, 8, 16, 8>(), osd_entry<512, 16, 16, 8>(),
         osd_entry<512, 8, 32, 8>(), osd_entry<512, 16, 32, 8>(),
     };
