@@ -714,6 +714,13 @@ def run_ours(args):
                 # issue slots used (the kernel is issue-bound; null if the summary is stale)
                 "issue_slots_used_frac": (lambda v: v / 100.0 if v is not None else None)(
                     profile_field("smsp__issue_active.avg.pct_of_peak_sustained_active"))}
+    # the op mix's own ceiling: 9 of the 13 operations (two-smallest 3, sign parity,
+    # magnitude select, sign apply, two clamp ops, syndrome XOR) run on the ALU pipe, which
+    # issues half the lanes (64/clk/SM); the other 4 fit in the FMA pipe's spare width
+    alu_ceiling = ops_per_edge_iter / 9 * 64 * sms * mhz * 1e6 / 1e12
+    roofline["alu_pipe_ceiling"] = {
+        "peak": alu_ceiling, "frac": achieved / alu_ceiling,
+        "basis": "9 of 13 ops per edge-iteration on the ALU pipe at 64 lanes/clk/SM"}
 
     # variants measured in the same run: FP16 messages and the plain baseline kernel
     variants = {}
