@@ -159,8 +159,9 @@ int pick_family(int dc, int dv, int fp16, const FusedKernel **tab, int *n) {
 // check rule does not depend on where an edge sits in its check, so every placement
 // gives the same messages.  Local search: swap two edges of one check when that
 // lowers the cost (equal-cost swaps are taken now and then, from a fixed LCG stream,
-// to leave plateaus); at most 8 sweeps.  bank(i, k) = bank of logical slot k of check i;
-// pos[e] = the logical slot of edge e.
+// to leave plateaus); at most 8 sweeps, and fewer on large graphs so that a create call
+// evaluates about 4 million swaps at most.  bank(i, k) = bank of logical slot k of check
+// i; pos[e] = the logical slot of edge e.
 template <typename BankFn>
 void place_edges(int M, int N, int DV, const int32_t *row_ptr, const int32_t *col_idx,
                  BankFn bank, std::vector<int> &pos) {
@@ -189,8 +190,14 @@ void place_edges(int M, int N, int DV, const int32_t *row_ptr, const int32_t *co
         --hist[(size_t)g * 32 + from];
         ++hist[(size_t)g * 32 + to];
     };
+    long long pairs = 0;
+    for (int i = 0; i < M; ++i) {
+        const long long d = row_ptr[i + 1] - row_ptr[i];
+        pairs += d * (d - 1) / 2;
+    }
+    const int sweeps = (int)std::max(1LL, std::min(8LL, 4000000LL / std::max(1LL, pairs)));
     uint32_t lcg = 12345u;
-    for (int sweep = 0; sweep < 8; ++sweep) {
+    for (int sweep = 0; sweep < sweeps; ++sweep) {
         int improved = 0;
         for (int i = 0; i < M; ++i)
             for (int a = row_ptr[i]; a < row_ptr[i + 1]; ++a)
