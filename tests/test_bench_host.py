@@ -1,0 +1,87 @@
+"""Host logic of the benchmark that its JSON line depends on (CPU only): the clock record
+taken during the timed region, and the fields read from the committed ncu summary, which
+must go null as soon as the kernel's sources differ from the ones the summary was taken on.
+"""
+import hashlib
+import os
+
+import pytest
+
+import bench
+
+
+class _Running:
+    """Stands in for the nvidia-smi process (summary() only checks that one existed)."""
+
+
+def _sampler(tmp_path, lines, skip):
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    with open(s.path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    s.proc = _Running()
+    s.skip = skip
+    return s
+
+
+def _row(mhz, max_mhz=2070, hw="Not Active", sw_pc="Not Active", thermal="Not Active"):
+    return f"0, {mhz}, {max_mhz}, 900.0, 0x0, {hw}, {thermal}, Not Active, {sw_pc}"
+
+
+def test_clock_summary_uses_samples_of_the_timed_region_only(tmp_path):
+    # the first two lines predate the timed region; one idle sample is ignored as unloaded
+    lines = [_row(345, hw="Active"), _row(345)] + [_row(2070)] * 5 + [_row(510)] + [_row(2055)]
+    s = _sampler(tmp_path, lines, skip=2)
+    out = s.summary()
+    assert out["samples"] == 7
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["sm_mhz"] == 2070.0           # median of the loaded samples
+    assert out["reasons"] == []              # hw_slowdown was active before the region only
+    assert not os.path.exists(s.path)
+
+
+def test_clock_summary_reports_throttle_reasons(tmp_path):
+    lines = [_row(1900, hw="Active"), _row(2070, sw_pc="Active"), _row(2070, thermal="Active")]
+    out = _sampler(tmp_path, lines, skip=0).summary()
+    assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_clock_summary_without_samples(tmp_path):
+    out = _sampler(tmp_path, [_row(2070)], skip=1).summary()
+    assert out["sm_mhz"] is None and out["reasons"] == ["no samples"]
+
+
+def _fake_tree(root, shots, rd, wr, issue):
+    csrc = root / "paper_2511_21660_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for k, name in enumerate(bench.KERNEL_SOURCES):
+        (csrc / name).write_text(f"// source {k}\n")
+    h = hashlib.sha1()
+    for name in bench.KERNEL_SOURCES:
+        h.update((csrc / name).read_bytes())
+    (root / "profiles").mkdir()
+    (root / "profiles" / "fused_decode_gross_T12.md").write_text(
+        "| metric | value | unit |\n|---|---|---|\n"
+        f"| kernel source sha1 (sources) | {h.hexdigest()[:12]} | |\n"
+        f"| shots per launch | {shots} | shots |\n"
+        f"| dram__bytes_read.sum | {rd} | byte |\n"
+        f"| dram__bytes_write.sum | {wr} | byte |\n"
+        f"| smsp__issue_active.avg.pct_of_peak_sustained_active | {issue} | % |\n")
+    return csrc
+
+
+def test_profile_fields_follow_the_kernel_source_hash(tmp_path, monkeypatch):
+    csrc = _fake_tree(tmp_path, 20000, 2_600_000, 4000, 75.5)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profile_field("smsp__issue_active.avg.pct_of_peak_sustained_active") == 75.5
+    # DRAM bytes scale from the summary's 20,000 shots to the benchmark's launch
+    assert bench.traffic_per_launch(None) == pytest.approx(2_604_000 * bench.SHOTS / 20000)
+    (csrc / bench.KERNEL_SOURCES[-1]).write_text("// changed\n")
+    assert bench.profile_field("smsp__issue_active.avg.pct_of_peak_sustained_active") is None
+    assert bench.traffic_per_launch(None) is None
+
+
+def test_profile_fields_absent_summary(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profile_field("anything") is None
+    assert bench.traffic_per_launch(None) is None
