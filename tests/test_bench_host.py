@@ -85,3 +85,31 @@ def test_profile_fields_absent_summary(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.profile_field("anything") is None
     assert bench.traffic_per_launch(None) is None
+
+
+def _run_reference(rank, tmp_path):
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank),
+               QLDPC_REF_SHOTS="40")
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl",
+                        "reference", "--steps", "1", "--warmup", "0", "--gpus", "2"],
+                       capture_output=True, text=True, env=env, cwd=str(tmp_path), timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [json.loads(line) for line in r.stdout.splitlines() if line.startswith("{")]
+
+
+def test_reference_arm_prints_one_line_on_rank_0(tmp_path):
+    lines = _run_reference(0, tmp_path)
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["unit"] == "syndromes/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "syndromes/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["n_gpus"] == 2
+
+
+def test_reference_arm_other_ranks_exit_without_work(tmp_path):
+    assert _run_reference(1, tmp_path) == []
