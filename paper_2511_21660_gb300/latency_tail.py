@@ -36,20 +36,21 @@ def condition(eps: float, C: int, t_ref: float, t_gen: float, t_max: float):
     return gamma < 1.0, L, gamma
 
 
-def max_code_blocks(eps: float, t_ref: float, t_gen: float, t_max: float) -> int:
-    """Largest C with eps * C * L < 1 (unbounded when eps = 0: returns a huge value)."""
+def max_code_blocks(eps: float, t_ref: float, t_gen: float, t_max: float):
+    """Largest C with eps * C * L < 1; None when eps = 0 (every C satisfies it)."""
     L = layers(t_ref, t_gen, t_max)
     if eps <= 0:
-        return 2**62
+        return None
     c = math.ceil(1.0 / (eps * L)) - 1
     return max(c, 0)
 
 
-def slowdown_bound(eps: float, C: int, t_ref: float, t_gen: float, t_max: float) -> float:
-    """1 + T_ref/T_gen + 2 gamma / (1 - gamma); inf when the requirement fails."""
+def slowdown_bound(eps: float, C: int, t_ref: float, t_gen: float, t_max: float):
+    """1 + T_ref/T_gen + 2 gamma / (1 - gamma); None when the requirement fails (the
+    derivation gives no bound there)."""
     ok, L, gamma = condition(eps, C, t_ref, t_gen, t_max)
     if not ok:
-        return math.inf
+        return None
     return 1.0 + t_ref / t_gen + 2.0 * gamma / (1.0 - gamma)
 
 

@@ -23,6 +23,10 @@ def test_layers_and_requirement_follow_the_equation():
     assert 5e-5 * C * 11 < 1 <= 5e-5 * (C + 1) * 11
     with pytest.raises(ValueError):
         lt.layers(1000, 1000, 6000)
+    # no tail: every number of code blocks satisfies the requirement
+    assert lt.max_code_blocks(0.0, 500, 1000, 6000) is None
+    # the requirement fails: the derivation gives no slowdown bound
+    assert lt.slowdown_bound(5e-5, 2000, 500, 1000, 6000) is None
 
 
 def test_slowdown_bound_with_no_tail_is_the_paper_value():
