@@ -157,26 +157,42 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # the reference arm: the CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------------------
-def cpu_oracle_rate(P, sig, gam, target_s: float = 10.0, precision: str = "f64"):
+ORACLE_TIMED_BUILD = "gcc -O3 -ffp-contract=off -fno-fast-math -fopenmp (oracle/build.py, f64_O3)"
+
+
+def cpu_oracle_rate(P, sig, gam, target_s: float = 8.0, precision: str = "f64_O3"):
+    """The FP64 oracle (the -O3 build of the same source, same values as the parity
+    build) timed on this host's cores twice: OpenMP over shots on every core, and on one
+    thread.  Each leg decodes a prefix of the benchmark's syndromes sized, from a short
+    calibration run, for about target_s seconds."""
     from oracle import build as oracle_build
     from oracle.relay import RelayParams, relay_decode
     oracle_build.build()
     prm = RelayParams(stop_after_solutions=S_SOLUTIONS)
     cores = os.cpu_count() or 1
-    cal = min(2000, sig.shape[0])
-    t0 = time.perf_counter()
-    relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig[:cal], prm, precision=precision,
-                 nthreads=cores)
-    dt = time.perf_counter() - t0
-    n = int(min(sig.shape[0], max(cal, cal * target_s / max(dt, 1e-6))))
-    t0 = time.perf_counter()
-    r = relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig[:n], prm, precision=precision,
-                     nthreads=cores)
-    dt = time.perf_counter() - t0
+
+    def leg(nthreads, cal):
+        cal = min(cal, sig.shape[0])
+        t0 = time.perf_counter()
+        relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig[:cal], prm, precision=precision,
+                     nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        n = int(min(sig.shape[0], max(cal, cal * target_s / max(dt, 1e-6))))
+        t0 = time.perf_counter()
+        r = relay_decode(P.row_ptr, P.col_idx, P.p, gam, sig[:n], prm, precision=precision,
+                         nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        return n, dt, float(P.E * r.iters.sum() / dt)
+
+    n, dt, eu = leg(cores, 2000)
+    n1, dt1, eu1 = leg(1, 200)
     return {"value": n / dt, "unit": "syndromes/s", "cores": cores, "kind": "oracle",
             "sample": f"first {n} of the {sig.shape[0]} syndromes, FP64 oracle, OpenMP over "
                       f"shots on {cores} host threads, {dt:.1f} s",
-            "edge_updates_per_s": float(P.E * r.iters.sum() / dt)}
+            "edge_updates_per_s": eu, "build": ORACLE_TIMED_BUILD,
+            "single_thread": {"value": n1 / dt1, "unit": "syndromes/s", "cores": 1,
+                              "sample": f"first {n1} syndromes on one thread, {dt1:.1f} s",
+                              "edge_updates_per_s": eu1}}
 
 
 def run_reference(args):
@@ -197,7 +213,8 @@ def run_reference(args):
         s = sig[off:off + per_step]
         off = (off + per_step) % (SHOTS - per_step)
         t0 = time.perf_counter()
-        relay_decode(P.row_ptr, P.col_idx, P.p, gam, s, prm, precision="f64", nthreads=cores)
+        relay_decode(P.row_ptr, P.col_idx, P.p, gam, s, prm, precision="f64_O3",
+                     nthreads=cores)
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
@@ -209,7 +226,7 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "shots_per_step": per_step, "S": S_SOLUTIONS,
                        "parallelism": "OpenMP over shots", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "syndromes/s", "cores": cores,
-                             "kind": "oracle",
+                             "kind": "oracle", "build": ORACLE_TIMED_BUILD,
                              "sample": f"{per_step} syndromes per step of the same workload"},
             "e2e": {"value": value, "unit": "syndromes/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -275,6 +292,64 @@ def traffic_per_launch(args):
     if not same_source or rd is None or wr is None or not shots:
         return None
     return (rd + wr) * SHOTS / shots
+
+
+def sm_max_mhz() -> float:
+    """Maximum SM clock measured on this machine (MEASURED_PEAKS.json), else the nominal
+    2070 MHz."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return 2070.0
+
+
+# Algorithmic work of one DMem-BP iteration of one shot (paper Sec. 2.3), per edge and
+# per fault: every edge's message is read and written by the check pass and by the fault
+# pass (4 accesses of the message size), every fault reads lambda(0), gamma and Lambda
+# and writes Lambda (16 B).  13 lane operations per edge: check node |nu|, two-smallest
+# update (3), sign parity, magnitude select, sign apply; fault node marginal add,
+# excluded-sum add, two clamp operations, the memory rule's share; the syndrome XOR.
+OPS_PER_EDGE_ITER = 13
+
+
+def smem_bytes_per_shot_iter(E: int, N: int, msg: str) -> int:
+    return (4 * (2 if msg == "fp16" else 4)) * E + 16 * N
+
+
+def decode_roofline(E, N, iters, ms, msg, sms, mhz, traffic=None):
+    """Roofline of a decode launch.  Shared memory moves 128 B/clock/SM and the SM
+    issues 128 lane-instructions/clock (4 schedulers x 32 lanes), at the maximum SM
+    clock: the smem roof is that bandwidth over the algorithmic bytes per edge-update,
+    the issue roof that rate over 13 operations per edge-update.  `frac` divides the
+    measured edge-updates/s by the lower roof (the smem roof for both message sizes),
+    i.e. algorithmic bytes/s over the shared-memory bandwidth."""
+    per_iter = smem_bytes_per_shot_iter(E, N, msg)
+    eu = E * iters / (ms / 1e3)
+    smem_peak = 128 * sms * mhz * 1e6                        # B/s
+    issue_peak = 128 * sms * mhz * 1e6                       # lane-instructions/s
+    smem_roof = smem_peak / (per_iter / E)
+    issue_roof = issue_peak / OPS_PER_EDGE_ITER
+    roof = min(smem_roof, issue_roof)
+    achieved = per_iter * iters / (ms / 1e3) / 1e9
+    ops = OPS_PER_EDGE_ITER * E * iters / (ms / 1e3)
+    # 9 of the 13 operations (two-smallest 3, sign parity, magnitude select, sign apply,
+    # two clamp ops, syndrome XOR) run on the ALU pipe, which issues 64 lanes/clock/SM
+    alu_ceiling = OPS_PER_EDGE_ITER / 9 * 64 * sms * mhz * 1e6
+    return {"bound": "smem" if smem_roof <= issue_roof else "alu",
+            "achieved": achieved, "peak": smem_peak / 1e9, "unit": "GB/s",
+            "frac": eu / roof, "traffic": traffic,
+            "peak_kind": "derived: 128 B/clk/SM x %d SMs x %.0f MHz (max SM clock)" % (sms, mhz),
+            "algorithmic": f"{per_iter} B per shot-iteration ({msg} messages: "
+                           f"{per_iter / E:.2f} B per edge-update) x {iters} iterations",
+            "edge_updates_per_s": eu, "smem_roof_edge_updates_per_s": smem_roof,
+            "issue_roof_edge_updates_per_s": issue_roof,
+            "issue_view": {"achieved_Tops": ops / 1e12, "peak_Tops": issue_peak / 1e12,
+                           "frac": ops / issue_peak,
+                           "basis": f"{OPS_PER_EDGE_ITER} algorithmic lane operations per "
+                                    "edge-update against 128 lanes/clk/SM"},
+            "alu_pipe_ceiling": {"peak_Tops": alu_ceiling / 1e12, "frac": ops / alu_ceiling,
+                                 "basis": "9 of 13 ops per edge-update on the ALU pipe at "
+                                          "64 lanes/clk/SM"}}
 
 
 def timed_decode(dec, syn, out, steps, warmup, stream, flush):
@@ -381,6 +456,14 @@ def post_processing_variants(args, dev, stream, flush, block_threads=0):
     ms_first = sum(timed_decode(first, syn, fo, 3, 3, stream, flush)) / 3
     ro = relay.outputs(n)
     ms_relay = sum(timed_decode(relay, syn, ro, 3, 2, stream, flush)) / 3
+    it_relay = ro[3].to(torch.int64)
+    # the paper's gross cutoff (Sec. 7.2): T_max = 6000 FPGA cycles = 3000 iterations at
+    # 2 cycles per iteration; a shot without a solution by then fails
+    cut = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam,
+                       RelayConfig(stop_after_solutions=S_SOLUTIONS, max_total_iters=3000,
+                                   block_threads=block_threads), device=dev.index)
+    co = cut.decode(syn, stream=stream)
+    torch.cuda.synchronize()
     skip = fo[2]
     ms_osd, cor, status, ncand = timed_post(osd, syn, fo[0], skip, stream, flush)
     ms_cl, cor_cl, st_cl, steps_cl = timed_post(cluster, syn, fo[0], skip, stream, flush)
@@ -392,6 +475,7 @@ def post_processing_variants(args, dev, stream, flush, block_threads=0):
         return ((F ^ bits).to(torch.float32) @ A.T).to(torch.int64).remainder(2).any(1)
     fail_first = (logical(cor) | ((skip == 0) & (status != QLDPC_OSD_SOLVED))).sum().item()
     fail_relay = (logical(ro[0]) | (ro[2] == 0)).sum().item()
+    fail_cut = (logical(co[0]) | (co[2] == 0)).sum().item()
     fail_cl = (logical(cor_cl) | ((skip == 0) & (st_cl != QLDPC_CLUSTER_DECODED))).sum().item()
     todo = int((skip == 0).sum().item())
     st = status[skip == 0]
@@ -406,6 +490,15 @@ def post_processing_variants(args, dev, stream, flush, block_threads=0):
            "mean_candidates": float(ncand[skip == 0].float().mean().item()) if todo else 0.0,
            "ler_first_leg_plus_osd": fail_first / n, "ler_relay_S5": fail_relay / n,
            "relay_ms": ms_relay,
+           "relay_iterations_per_shot": {"mean": float(it_relay.double().mean().item()),
+                                         "p99": float(torch.quantile(it_relay.double(), 0.99)),
+                                         "max": int(it_relay.max().item()),
+                                         "shots_at_the_18080_bound":
+                                             int((it_relay >= 80 + 300 * 60).sum().item())},
+           # the same decode's roofline (the hard regime: many iterations per leg end)
+           "relay_roofline": decode_roofline(P.E, P.N, int(it_relay.sum().item()), ms_relay,
+                                             "fp32", relay.info.num_sms, sm_max_mhz()),
+           "ler_relay_S5_cutoff_3000_iterations": fail_cut / n,
            # Sec. 2.2 / 7.2 conditions on full Relay's measured iteration counts at this
            # noise rate, in FPGA cycles at 2 per iteration (T_ref 500, T_gen 1000, 6000)
            "relay_latency_tail": {k: v for k, v in latency_tail.report(
@@ -445,7 +538,7 @@ def post_processing_variants(args, dev, stream, flush, block_threads=0):
             "value": sig.shape[0] / dt, "unit": "post-processed shots/s",
             "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"the first {sig.shape[0]} unconverged shots"}
-    for d in (first, relay, osd, cluster):
+    for d in (first, relay, cut, osd, cluster):
         d.close()
     return out
 
@@ -683,44 +776,14 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    # roofline of the decode kernel.  The kernel is bound by instruction issue (the
-    # profile shows the ALU pipe and issue slots as the busiest units, DRAM idle), so
-    # the figure is algorithmic lane-operations per second against the derived ALU
-    # peak: 13 operations per edge per iteration (check node: |nu|, the two-smallest
-    # update (3), sign parity, magnitude select, sign apply = 7; fault node: marginal
-    # add, excluded-sum add, two clamp ops, memory-term share = 5; syndrome XOR = 1).
-    ops_per_edge_iter = 13
-    alg_ops = ops_per_edge_iter * P.E * total_iters
-    achieved = alg_ops / (ms / 1e3) / 1e12
+    # roofline of the decode kernel (shared-memory roof of the algorithmic message and
+    # fault-state bytes, the lower of the two roofs; issue and ALU-pipe views beside it)
     sms = dec.info.num_sms
-    # 128 lanes/clk/SM (4 schedulers x 32) at the maximum SM clock measured on this machine
-    # (MEASURED_PEAKS.json), else the nominal 2070 MHz
-    mhz = 2070.0
-    try:
-        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
-    except (OSError, ValueError, KeyError, TypeError):
-        pass
-    peak = 128 * sms * mhz * 1e6 / 1e12
-    smem_bytes = 4 * 4 * P.E * total_iters   # read nu, write mu, read mu, write nu (float32)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": traffic_per_launch(args),
-                "peak_kind": "derived: 128 lanes/clk/SM x %d SMs x %.0f MHz (max SM clock)" % (sms, mhz),
-                "algorithmic": f"{ops_per_edge_iter} ops x E={P.E} x {total_iters} iterations "
-                               f"= {alg_ops / 1e9:.1f} G ops per launch",
-                "smem_message_bytes_per_launch": smem_bytes,
-                "smem_GBps": smem_bytes / (ms / 1e3) / 1e9,
-                "smem_peak_GBps": 128 * sms * mhz * 1e6 / 1e9,
-                # executed-instruction view from the same ncu summary: the fraction of
-                # issue slots used (the kernel is issue-bound; null if the summary is stale)
-                "issue_slots_used_frac": (lambda v: v / 100.0 if v is not None else None)(
-                    profile_field("smsp__issue_active.avg.pct_of_peak_sustained_active"))}
-    # the op mix's own ceiling: 9 of the 13 operations (two-smallest 3, sign parity,
-    # magnitude select, sign apply, two clamp ops, syndrome XOR) run on the ALU pipe, which
-    # issues half the lanes (64/clk/SM); the other 4 fit in the FMA pipe's spare width
-    alu_ceiling = ops_per_edge_iter / 9 * 64 * sms * mhz * 1e6 / 1e12
-    roofline["alu_pipe_ceiling"] = {
-        "peak": alu_ceiling, "frac": achieved / alu_ceiling,
-        "basis": "9 of 13 ops per edge-iteration on the ALU pipe at 64 lanes/clk/SM"}
+    mhz = sm_max_mhz()
+    roofline = decode_roofline(P.E, P.N, total_iters, ms, "fp32", sms, mhz,
+                               traffic=traffic_per_launch(args))
+    roofline["issue_slots_used_frac"] = (lambda v: v / 100.0 if v is not None else None)(
+        profile_field("smsp__issue_active.avg.pct_of_peak_sustained_active"))
 
     # variants measured in the same run: FP16 messages and the plain baseline kernel
     variants = {}
@@ -741,6 +804,10 @@ def run_ours(args):
                           "ms_per_step": vms, "block_threads": vd.info.block_threads,
                           "blocks_per_sm": vd.info.blocks_per_sm,
                           "identical_to_fp32_fused": same}
+        if name == "fused_fp16":
+            it16 = int(vo[3].to(torch.int64).sum().item())
+            variants[name]["roofline"] = decode_roofline(P.E, P.N, it16, vms, "fp16", sms, mhz)
+            variants[name]["speedup_vs_fused_fp32"] = ms / vms
         vd.close()
     variants["fused_fp32_speedup_vs_baseline"] = (value / ws) / variants["baseline_fp32"]["value"]
 
@@ -808,7 +875,12 @@ def run_ours(args):
                           "gross_cutoff_cycles": 6000, "gross_ler_at_cutoff": 4e-7,
                           "tail_fraction_beyond_500_cycles_gross": 5e-5,
                           "single_instance_syndromes_per_s_upper_bound": 1.7e5},
-        "roofline": roofline, "variants": variants, "e2e": e2e, "cpu_baseline": cpu,
+        "roofline": roofline,
+        # the same kernel in the hard regime (p = 0.02, full Relay, S = 5, 10^5 shots)
+        "roofline_hard_regime": {
+            "workload": "gross T=12 phenomenological p=0.02, 10^5 shots, S=5, float32",
+            **variants["first_leg_then_post_processing"]["relay_roofline"]},
+        "variants": variants, "e2e": e2e, "cpu_baseline": cpu,
         "clocks": clocks, "gpu_launches": args.steps,
         "wall_s_timed_region": t_wall,
     }

@@ -1,8 +1,11 @@
 """Compile the C oracle into shared libraries under oracle/_build/.
 
-Three builds of the same source: the FP64 oracle, its single-precision mirror
-and the mirror whose fault->check messages are stored in binary16.  Plain gcc,
-OpenMP over shots, no contraction of multiply-add (-ffp-contract=off).
+Builds of the same source: the FP64 oracle, its single-precision mirror and the
+mirror whose fault->check messages are stored in binary16 (-O2, used by the tests),
+plus the FP64 oracle at -O3 (f64_O3), the build the benchmark times as its CPU
+baseline.  Plain gcc, OpenMP over shots, no contraction of multiply-add
+(-ffp-contract=off) and no fast-math, so the -O3 build computes the same values as
+the -O2 one.  No -march=native: the same host code runs on x86 and Arm hosts.
 """
 from __future__ import annotations
 
@@ -17,6 +20,7 @@ VARIANTS = {
     "f64": [],
     "f32": ["-DREAL=float"],
     "f16s": ["-DREAL=float", "-DMSG_FP16"],
+    "f64_O3": ["-O3"],   # the last -O flag wins
 }
 SOURCES = {"relay": "relay_oracle.c", "soft": "soft_dmem_oracle.c"}
 

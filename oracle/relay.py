@@ -81,7 +81,8 @@ def relay_decode(row_ptr, col_idx, priors, gamma, sigma, params: RelayParams,
     """Decode syndromes sigma (uint8 [B, M]) with Relay.
 
     precision: "f64" (the oracle), "f32" (single-precision mirror) or "f16s"
-    (single precision with binary16 message storage).
+    (single precision with binary16 message storage); "f64_O3" is the FP64 oracle
+    compiled at -O3 (same values, the benchmark's timed CPU baseline).
     nthreads: OpenMP threads over shots (0 = all host cores).
     """
     row_ptr, col_idx = _csr(row_ptr, col_idx)

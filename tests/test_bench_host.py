@@ -113,3 +113,36 @@ def test_reference_arm_prints_one_line_on_rank_0(tmp_path):
 
 def test_reference_arm_other_ranks_exit_without_work(tmp_path):
     assert _run_reference(1, tmp_path) == []
+
+
+def test_decode_roofline_follows_the_shared_memory_and_issue_roofs():
+    """Gross T=12 (E = 7344, N = 2736), 561,398 iterations in 7.718 ms on 152 SMs at
+    2070 MHz: 161,280 B per shot-iteration in float32 (16 B per edge, 16 B per fault), so
+    the smem roof is 40.27 TB/s / 21.96 B = 1.834e12 edge-updates/s, below the issue roof
+    of 40.27e12 / 13 = 3.098e12; binary16 moves 102,528 B and its smem roof is 2.885e12."""
+    r = bench.decode_roofline(7344, 2736, 561398, 7.718, "fp32", 152, 2070.0)
+    assert bench.smem_bytes_per_shot_iter(7344, 2736, "fp32") == 161280
+    assert bench.smem_bytes_per_shot_iter(7344, 2736, "fp16") == 102528
+    assert r["bound"] == "smem" and r["unit"] == "GB/s"
+    assert r["peak"] == pytest.approx(40273.92)
+    assert r["smem_roof_edge_updates_per_s"] == pytest.approx(40.27392e12 / (161280 / 7344))
+    assert r["issue_roof_edge_updates_per_s"] == pytest.approx(40.27392e12 / 13)
+    eu = 7344 * 561398 / 7.718e-3
+    assert r["edge_updates_per_s"] == pytest.approx(eu)
+    assert r["frac"] == pytest.approx(eu / r["smem_roof_edge_updates_per_s"])
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert 0.28 < r["frac"] < 0.30
+    assert r["issue_view"]["frac"] == pytest.approx(13 * eu / 40.27392e12)
+    h = bench.decode_roofline(7344, 2736, 561515, 7.42, "fp16", 152, 2070.0)
+    assert h["bound"] == "smem" and h["smem_roof_edge_updates_per_s"] == pytest.approx(
+        40.27392e12 / (102528 / 7344))
+    assert h["frac"] == pytest.approx(h["achieved"] / h["peak"])
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    P, sig, gam = bench.make_inputs(400, 1)
+    r = bench.cpu_oracle_rate(P, sig, gam, target_s=0.05)
+    assert r["kind"] == "oracle" and r["cores"] == (os.cpu_count() or 1) and r["value"] > 0
+    assert "-O3" in r["build"] and "-ffp-contract=off" in r["build"]
+    one = r["single_thread"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["edge_updates_per_s"] > 0

@@ -255,3 +255,27 @@ def test_precision_mirrors_track_fp64():
         assert err.max() < tol, (prec, err.max())
         if prec == "f16s":
             assert (nu.astype(np.float16).astype(np.float64) == nu).all()
+
+
+# --------------------------------------------------------------------------------------
+# The benchmark's timed build (-O3) computes exactly what the parity build computes
+# --------------------------------------------------------------------------------------
+def test_timed_O3_build_equals_the_parity_build():
+    """oracle/build.py's f64_O3 library (the CPU baseline the benchmark times) keeps
+    -ffp-contract=off and no fast-math, so every output equals the -O2 build's, on
+    gross-code shots at p = 0.02 that run many legs, with final marginals compared bit
+    for bit and a single thread against all threads."""
+    P = phenomenological_dem(BB144, 12, 0.02)
+    F = sample_faults(P.p, 4, 48)
+    s = syndromes_of(P.row_ptr, P.col_idx, F)
+    gam = gamma_table(P.N, 300, 0.125, -0.24, 0.66, 4)
+    prm = RelayParams(stop_after_solutions=5, max_total_iters=600)
+    a = relay_decode(P.row_ptr, P.col_idx, P.p, gam, s, prm, precision="f64",
+                     want_marginals=True)
+    b = relay_decode(P.row_ptr, P.col_idx, P.p, gam, s, prm, precision="f64_O3",
+                     want_marginals=True, nthreads=1)
+    assert a.legs.max() > 2
+    for x, y in ((a.corrections, b.corrections), (a.legs, b.legs), (a.converged, b.converged),
+                 (a.iters, b.iters)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.final_marginals.view(np.uint64), b.final_marginals.view(np.uint64))
