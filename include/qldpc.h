@@ -178,13 +178,15 @@ int qldpc_decode_batch_grouped(qldpc_decoder *const *decoders, int32_t n_codes,
  * its staging buffers on first use and whenever the batch grows.)
  * The syndromes, outputs and the kernel's work counter are staged in one static
  * device array of QLDPC_STATIC_SCRATCH_BYTES; a batch must fit in it (for the gross
- * code, 936 x 2736, about 17,000 shots per call), else INVALID_ARG names the limit.
+ * code, 936 x 2736, 17,732 shots per call), else INVALID_ARG names the exact limit.
  * Host pointers as in qldpc_decode_batch_host; synchronous on the handle's internal
- * stream.  The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call on a device
- * shares the one array, which keeps the previous call's contents (the work counter
- * is cleared by each call): calls that overlap on the GPU, from any handle, race.
- * Fused kernel only (UNSUPPORTED for the baseline kernel).
+ * stream.  qldpc_create looks up the array's device address in the context current
+ * at creation (the first create on a device makes the driver load the array there)
+ * and keeps it in the handle, so calls themselves load and allocate nothing; like
+ * every handle, one created before a cudaDeviceReset must not be used after it.
+ * Every call on a device shares the one array, which keeps the previous call's
+ * contents (the work counter is cleared by each call): calls that overlap on the GPU,
+ * from any handle, race.  Fused kernel only (UNSUPPORTED for the baseline kernel).
  */
 int qldpc_decode_batch_host_static(qldpc_decoder *d, const uint64_t *syndromes, int64_t B,
                                    uint64_t *corrections, int32_t *legs_used,

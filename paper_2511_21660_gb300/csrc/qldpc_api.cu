@@ -5,7 +5,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -75,7 +74,12 @@ struct qldpc_decoder {
     cudaStream_t stream = nullptr;  // internal stream of the host-buffer entry point
     void *stage = nullptr;
     int64_t stage_B = 0;
+    unsigned char *static_scratch = nullptr;  // device address of the static staging array
 };
+
+namespace {
+int lookup_static_scratch(qldpc_decoder *d);
+}
 
 namespace {
 
@@ -461,6 +465,7 @@ int qldpc_create(qldpc_decoder **out, int32_t M, int32_t N, const int32_t *row_p
         cudaError_t e = cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) rc = fail(QLDPC_ERR_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
     }
+    if (rc == QLDPC_OK && d->kernel == QLDPC_KERNEL_FUSED) rc = lookup_static_scratch(d);
     if (rc != QLDPC_OK) {
         std::string msg = g_last_error;
         qldpc_destroy(d);
@@ -542,23 +547,32 @@ static __device__ __align__(256) unsigned char g_static_scratch[QLDPC_STATIC_SCR
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mutex;
-void *g_static_ptr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device (looked up once per
-// device; the host-side symbol is only a stand-in and must not reach a kernel).
-int static_scratch(int device, unsigned char **out) {
-    if (device < 0 || device >= kMaxDevices)
-        return fail(QLDPC_ERR_UNSUPPORTED, "device ordinal %d above %d", device, kMaxDevices - 1);
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_ptr[device]) {
-        void *p = nullptr;
-        QL_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
-        g_static_ptr[device] = p;
-    }
-    *out = static_cast<unsigned char *>(g_static_ptr[device]);
+// Device address of g_static_scratch in the context current at set-up (qldpc_create,
+// with the handle's device current).  Host code must not hand the symbol itself to a
+// kernel: on the host it is only a stand-in.  Keeping the address in the handle ties it
+// to the context the handle lives in; a handle does not outlive a cudaDeviceReset.
+int lookup_static_scratch(qldpc_decoder *d) {
+    void *p = nullptr;
+    QL_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    d->static_scratch = static_cast<unsigned char *>(p);
     return QLDPC_OK;
+}
+
+// Bytes of the static array a batch of B shots takes: the work counter, then syndromes,
+// corrections, legs, iterations and converged flags, each 256-byte aligned.
+size_t static_need(int sw, int cw, int64_t B) {
+    return 256 + align_up(8 * (size_t)sw * B, 256) + align_up(8 * (size_t)cw * B, 256) +
+           2 * align_up(4 * (size_t)B, 256) + align_up((size_t)B, 256);
+}
+
+// Largest batch that fits the static array (static_need grows with B).
+int64_t static_max_shots(int sw, int cw) {
+    int64_t lo = 0, hi = (int64_t)QLDPC_STATIC_SCRATCH_BYTES;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (static_need(sw, cw, mid) <= (size_t)QLDPC_STATIC_SCRATCH_BYTES) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 }  // namespace
@@ -576,20 +590,19 @@ extern "C" int qldpc_decode_batch_host_static(qldpc_decoder *d, const uint64_t *
     const int sw = (d->M + 63) / 64, cw = (d->N + 63) / 64;
     const size_t s_cnt = 256, s_syn = align_up(8 * (size_t)sw * B, 256);
     const size_t s_cor = align_up(8 * (size_t)cw * B, 256);
-    const size_t s_i32 = align_up(4 * (size_t)B, 256), s_u8 = align_up((size_t)B, 256);
-    const size_t need = s_cnt + s_syn + s_cor + 2 * s_i32 + s_u8;
+    const size_t s_i32 = align_up(4 * (size_t)B, 256);
+    const size_t need = static_need(sw, cw, B);
     if (need > (size_t)QLDPC_STATIC_SCRATCH_BYTES)
         return fail(QLDPC_ERR_INVALID_ARG,
                     "a batch of %lld shots needs %zu bytes of static scratch, above the %d-byte "
                     "maximum (at most %lld shots of this code per call)",
                     (long long)B, need, QLDPC_STATIC_SCRATCH_BYTES,
-                    (long long)(((size_t)QLDPC_STATIC_SCRATCH_BYTES - s_cnt - 6 * 256) /
-                                (8 * (size_t)(sw + cw) + 9)));
+                    (long long)static_max_shots(sw, cw));
+    if (!d->static_scratch)
+        return fail(QLDPC_ERR_UNSUPPORTED, "the handle has no static scratch address");
     DeviceGuard guard(d->device);
     QL_CUDA(guard.err);
-    unsigned char *base = nullptr;
-    rc = static_scratch(d->device, &base);
-    if (rc) return rc;
+    unsigned char *base = d->static_scratch;
     unsigned int *counter = reinterpret_cast<unsigned int *>(base);
     uint64_t *dsyn = reinterpret_cast<uint64_t *>(base + s_cnt);
     uint64_t *dcor = reinterpret_cast<uint64_t *>(base + s_cnt + s_syn);
