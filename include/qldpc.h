@@ -65,6 +65,12 @@ typedef struct {
     const float *gamma_table;     /* host, [(R+1)][N] row-major: row r holds the memory
                                      strengths gamma_j of leg r+1 (row 0 = first leg).
                                      Copied at create time; finite values required.        */
+    int32_t tail_cut_iters;       /* tail continuation of the fused kernel: a shot that has
+                                     run this many iterations when a leg ends, with a next
+                                     leg to run, is handed to a second launch with one
+                                     1024-thread block per SM (same results, lower latency
+                                     for the few very long shots).  0: T_1 + 8 T_r;
+                                     < 0: off                                              */
 } qldpc_relay_params;
 
 typedef struct qldpc_decoder qldpc_decoder; /* opaque */
@@ -82,6 +88,11 @@ typedef struct {
     int32_t smem_bytes;           /* dynamic shared memory per block                         */
     int32_t syndrome_words;       /* ceil(M/64): uint64 words per syndrome                   */
     int32_t correction_words;     /* ceil(N/64): uint64 words per correction                 */
+    int32_t tail_cut_iters;       /* iterations before a shot may move to the second launch
+                                     (-1: no tail continuation)                             */
+    int32_t tail_block_threads;   /* block size of the second launch                        */
+    int32_t tail_records;         /* shots the second launch can take per call; later long
+                                     shots finish in the first launch                       */
 } qldpc_info;
 
 /*

@@ -70,7 +70,12 @@ struct qldpc_decoder {
     FusedGraph fg{};
     BaseGraph bg{};
     void *arena = nullptr;
-    unsigned int *counter = nullptr;
+    unsigned int *counter = nullptr;  // [0] work counter, [1] tail records, [2] records taken
+    // tail continuation (fused kernel): the resuming launch's kernel and grid, the records
+    const FusedKernel *fk_tail = nullptr;
+    int tail_grid = 0;
+    TailCont tail{};  // mode 0 when off
+    void *tail_arena = nullptr;
     cudaStream_t stream = nullptr;  // internal stream of the host-buffer entry point
     void *stage = nullptr;
     int64_t stage_B = 0;
@@ -226,8 +231,41 @@ void place_edges(int M, int N, int DV, const int32_t *row_ptr, const int32_t *co
     }
 }
 
+// Tail continuation: the resuming launch runs the compiled 1024-thread shape with the
+// fewest faults per thread that holds N (one block per SM; none holds it: no
+// continuation); 4 records per SM.  tail_cut < 0 turns it off, 0 picks T_1 + 8 T_r.
+int setup_tail(qldpc_decoder *d, const FusedKernel *tab, int ntab, int tail_cut) {
+    if (tail_cut < 0) return QLDPC_OK;
+    for (int q = 0; q < ntab; ++q)
+        if (tab[q].resume_fn && (long long)tab[q].threads * tab[q].vpt >= d->N &&
+            (!d->fk_tail || tab[q].vpt < d->fk_tail->vpt))
+            d->fk_tail = &tab[q];
+    if (!d->fk_tail) return QLDPC_OK;  // no resuming shape holds the graph
+    QL_CUDA(cudaFuncSetAttribute(d->fk_tail->resume_fn,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem));
+    int bps = 0;
+    QL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, d->fk_tail->resume_fn,
+                                                          d->fk_tail->threads, d->smem));
+    if (bps < 1) {  // not resident: no continuation
+        d->fk_tail = nullptr;
+        return QLDPC_OK;
+    }
+    d->tail_grid = d->num_sms * bps;
+    TailCont &tc = d->tail;
+    tc.cap = 4 * d->num_sms;
+    tc.cut = tail_cut > 0 ? tail_cut : (long long)d->prm.T1 + 8LL * d->prm.T2;
+    const size_t rec_bytes = align_up(sizeof(TailRecord) * (size_t)tc.cap, 256);
+    QL_CUDA(cudaMalloc(&d->tail_arena, rec_bytes + sizeof(float) * (size_t)tc.cap * d->N));
+    tc.rec = static_cast<TailRecord *>(d->tail_arena);
+    tc.lam = reinterpret_cast<float *>(static_cast<char *>(d->tail_arena) + rec_bytes);
+    tc.count = d->counter + 1;
+    tc.mode = 1;
+    return QLDPC_OK;
+}
+
 int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx,
-                const std::vector<float> &w, const float *gamma, int block_threads) {
+                const std::vector<float> &w, const float *gamma, int block_threads,
+                int tail_cut) {
     const int M = d->M, N = d->N, E = d->E;
     const FusedKernel *tab = nullptr;
     int ntab = 0;
@@ -337,7 +375,7 @@ int setup_fused(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx
     g.slot_edge = reinterpret_cast<const int32_t *>(base + off[6]);
     d->counter = reinterpret_cast<unsigned int *>(base + off[7]);
     QL_CUDA(cudaMemset(d->counter, 0, sizeof(unsigned int) * 4));
-    return QLDPC_OK;
+    return setup_tail(d, tab, ntab, tail_cut);
 }
 
 int setup_baseline(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_idx,
@@ -394,17 +432,32 @@ int setup_baseline(qldpc_decoder *d, const int32_t *row_ptr, const int32_t *col_
     return QLDPC_OK;
 }
 
+// The persistent decode over the shots of `map`, with the tail continuation when the
+// handle has one: the first launch (work counter `counter`, zeroed here) suspends long
+// shots into the handle's records, the second launch (one block per SM of the tail
+// shape) finishes them.  Both on `st`, so the pair can be captured in a CUDA graph.
+int launch_persistent(const qldpc_decoder *d, const uint64_t *syn, int64_t B, DecodeOut out,
+                      unsigned int *counter, ShotMap map, cudaStream_t st) {
+    const bool tail = d->fk_tail != nullptr;
+    QL_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), st));
+    if (tail) QL_CUDA(cudaMemsetAsync(d->counter + 1, 0, 2 * sizeof(unsigned int), st));
+    const int grid = (int)std::min<int64_t>(d->grid, B);
+    QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, syn, (int)B, out,
+                                 counter, map, d->tail));
+    if (tail)
+        QL_CUDA(d->fk_tail->launch_resume(dim3(std::min(d->tail_grid, d->tail.cap)), d->smem, st,
+                                          d->fg, d->prm, syn, (int)B, out, d->counter + 2, map,
+                                          d->tail));
+    return QLDPC_OK;
+}
+
 int launch(qldpc_decoder *d, const uint64_t *syn, int64_t B, DecodeOut out, cudaStream_t st) {
     if (d->kernel == QLDPC_KERNEL_BASELINE) {
         QL_CUDA(launch_baseline((int)B, d->block_threads, d->smem, st, d->bg, d->prm, syn, out));
         return QLDPC_OK;
     }
-    QL_CUDA(cudaMemsetAsync(d->counter, 0, sizeof(unsigned int), st));
-    const int grid = (int)std::min<int64_t>(d->grid, B);
-    QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, syn, (int)B, out,
-                                 d->counter, ShotMap{nullptr, nullptr, d->fg.syn_words,
-                                                     d->fg.cor_words}));
-    return QLDPC_OK;
+    return launch_persistent(d, syn, B, out, d->counter,
+                             ShotMap{nullptr, nullptr, d->fg.syn_words, d->fg.cor_words}, st);
 }
 
 int check_batch(const qldpc_decoder *d, const void *syn, int64_t B, const void *corr) {
@@ -460,7 +513,8 @@ int qldpc_create(qldpc_decoder **out, int32_t M, int32_t N, const int32_t *row_p
 
     rc = d->kernel == QLDPC_KERNEL_BASELINE
              ? setup_baseline(d, row_ptr, col_idx, w, prm->gamma_table)
-             : setup_fused(d, row_ptr, col_idx, w, prm->gamma_table, prm->block_threads);
+             : setup_fused(d, row_ptr, col_idx, w, prm->gamma_table, prm->block_threads,
+                           prm->tail_cut_iters);
     if (rc == QLDPC_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) rc = fail(QLDPC_ERR_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
@@ -611,12 +665,11 @@ extern "C" int qldpc_decode_batch_host_static(qldpc_decoder *d, const uint64_t *
     uint8_t *dconv = reinterpret_cast<uint8_t *>(base + s_cnt + s_syn + s_cor + 2 * s_i32);
     cudaStream_t st = d->stream;
     QL_CUDA(cudaMemcpyAsync(dsyn, syndromes, 8 * (size_t)sw * B, cudaMemcpyHostToDevice, st));
-    QL_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned int), st));  // the work counter starts at 0
-    const int grid = (int)std::min<int64_t>(d->grid, B);
-    QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, dsyn, (int)B,
-                                 DecodeOut{dcor, legs_used ? dlegs : nullptr,
-                                           converged ? dconv : nullptr, iters ? diters : nullptr},
-                                 counter, ShotMap{nullptr, nullptr, sw, cw}));
+    rc = launch_persistent(d, dsyn, B,
+                           DecodeOut{dcor, legs_used ? dlegs : nullptr, converged ? dconv : nullptr,
+                                     iters ? diters : nullptr},
+                           counter, ShotMap{nullptr, nullptr, sw, cw}, st);
+    if (rc) return rc;
     QL_CUDA(cudaMemcpyAsync(corrections, dcor, 8 * (size_t)cw * B, cudaMemcpyDeviceToHost, st));
     if (legs_used) QL_CUDA(cudaMemcpyAsync(legs_used, dlegs, 4 * (size_t)B, cudaMemcpyDeviceToHost, st));
     if (iters) QL_CUDA(cudaMemcpyAsync(iters, diters, 4 * (size_t)B, cudaMemcpyDeviceToHost, st));
@@ -778,12 +831,11 @@ int qldpc_decode_batch_grouped(qldpc_decoder *const *decoders, int32_t n_codes,
     for (int q = 0; q < n_codes; ++q) {
         const int c = order[q];
         qldpc_decoder *d = decoders[c];
-        QL_CUDA(cudaMemsetAsync(d->counter, 0, sizeof(unsigned int), st));
-        const int grid = (int)std::min<int64_t>(d->grid, B);
-        QL_CUDA(d->fk->launch_decode(dim3(grid), d->smem, st, d->fg, d->prm, syndromes, (int)B,
-                                     out, d->counter,
-                                     ShotMap{lists + (size_t)c * B, counts + c, syndrome_stride,
-                                             correction_stride}));
+        const int rc = launch_persistent(d, syndromes, B, out, d->counter,
+                                         ShotMap{lists + (size_t)c * B, counts + c,
+                                                 syndrome_stride, correction_stride},
+                                         st);
+        if (rc) return rc;
     }
     return QLDPC_OK;
 }
@@ -825,6 +877,9 @@ int qldpc_get_info(const qldpc_decoder *d, qldpc_info *info) {
     info->smem_bytes = (int32_t)d->smem;
     info->syndrome_words = (d->M + 63) / 64;
     info->correction_words = (d->N + 63) / 64;
+    info->tail_cut_iters = d->fk_tail ? (int32_t)d->tail.cut : -1;
+    info->tail_block_threads = d->fk_tail ? d->fk_tail->threads : 0;
+    info->tail_records = d->fk_tail ? d->tail.cap : 0;
     return QLDPC_OK;
 }
 
@@ -836,6 +891,7 @@ void qldpc_destroy(qldpc_decoder *d) {
         cudaStreamDestroy(d->stream);
     }
     if (d->arena) cudaFree(d->arena);  // cudaFree waits for work that may still use it
+    if (d->tail_arena) cudaFree(d->tail_arena);
     if (d->stage) cudaFree(d->stage);
     delete d;
 }
@@ -1101,6 +1157,7 @@ int create_plain_bp(qldpc_decoder **out, int32_t M, int32_t N, const int32_t *ro
                     const int32_t *col_idx, const double *priors, int bp_iters, int device) {
     std::vector<float> zeros((size_t)N, 0.0f);
     qldpc_relay_params rp{};
+    rp.tail_cut_iters = -1;
     rp.legs_after_first = 0;
     rp.iters_first = bp_iters > 0 ? bp_iters : 1;
     rp.iters_later = 1;

@@ -80,6 +80,32 @@ struct ShotMap {
     int syn_stride, cor_stride;
 };
 
+// Tail continuation of a persistent decode (two launches on one stream).  The first
+// launch (mode 1) suspends a shot at a leg boundary once it has run `cut` iterations and
+// a next leg would start: the shot's Relay state at that boundary goes to record k of
+// the list (k from *count; at most cap records, later candidates go on decoding in the
+// first launch) and its outputs are left to the second launch (mode 2), which takes the
+// records in turn with a wider block shape, restores the state and finishes the shots.
+// The kept solution of a suspended shot is already in its correction row.  Mode 0: no
+// continuation.  A leg boundary holds the whole state of Relay, so both paths give the
+// same results.  The second launch runs the kernel's RESUME instance.
+struct TailRecord {
+    int32_t shot;
+    int32_t leg;          // the leg that starts when the shot resumes
+    int32_t sols;         // solutions found so far
+    int32_t have;         // 1: a solution is kept (in the shot's correction row)
+    long long iters;      // iterations run so far
+    long long Wbest;      // weight of the kept solution (2^-33 units)
+};
+struct TailCont {
+    int mode;             // 0 none, 1 suspend long shots (the second launch ignores it)
+    int cap;              // records available
+    long long cut;        // iterations before a shot may be suspended (mode 1)
+    TailRecord *rec;      // [cap]
+    float *lam;           // [cap][N] Lambda of each suspended shot at its boundary
+    unsigned int *count;  // suspension candidates so far (records used: min(count, cap))
+};
+
 // One compiled instance of the fused kernel.
 struct FusedKernel {
     int msg_fp16;   // 0 float32 storage, 1 binary16 storage
@@ -90,7 +116,11 @@ struct FusedKernel {
     const void *decode_fn;   // __global__ symbol of the decode kernel
     cudaError_t (*launch_decode)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                                  const DevParams &p, const uint64_t *syn, int B, DecodeOut out,
-                                 unsigned int *counter, ShotMap map);
+                                 unsigned int *counter, ShotMap map, TailCont tc);
+    const void *resume_fn;   // __global__ symbol of the resuming instance (nullptr if none)
+    cudaError_t (*launch_resume)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
+                                 const DevParams &p, const uint64_t *syn, int B, DecodeOut out,
+                                 unsigned int *counter, ShotMap map, TailCont tc);
     const void *multi_fn;    // __global__ symbol of the mixed-batch kernel
     cudaError_t (*launch_multi)(dim3 grid, size_t smem, cudaStream_t st, const MultiTable &tab,
                                 const int32_t *code_of_shot, const uint64_t *syn,

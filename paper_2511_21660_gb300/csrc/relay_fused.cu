@@ -43,21 +43,46 @@ namespace {
 // new solution adds into); the other one is zeroed after each use, at least two
 // barriers before it is added into again.  Both start at zero and ab persists across
 // the block's shots.
-template <typename MT, int NT, int VPT, int DC, int DV, bool SKIP = false>
+// Tail continuation (TailCont): with tc.mode 1 a shot that reaches a leg boundary after
+// tc.cut iterations, with a next leg to run, may be suspended (its state saved in a
+// record, no outputs written); rec >= 0 resumes the shot of record rec at its boundary.
+// s_slot: a shared int that broadcasts the record taken for a suspension.
+template <typename MT, int NT, int VPT, int DC, int DV, bool SKIP = false, bool RESUME = false>
 __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams &p, int shot,
                                             const uint64_t *sy, uint64_t *cor, DecodeOut out,
                                             unsigned char *msg, uint32_t *fw, uint32_t *fb,
                                             uint32_t *sg, uint32_t *par, float *ws,
                                             long long *wacc,
                                             float (&Lam)[VPT], float (&bb)[VPT],
-                                            float (&gg)[VPT], int &ab) {
+                                            float (&gg)[VPT], int &ab, const TailCont &tc,
+                                            int rec, int *s_slot) {
     const int tid = threadIdx.x;
     const float C = p.clip;
     load_syndrome<NT>(g, sy, sg);
     int leg = 0, sols = 0, t = 0, pb = 0;
     long long iters = 0, Wbest = 0;
     bool have = false;
-    leg_init<MT, NT, VPT, DV, SKIP>(g, p, 0, msg, ws, Lam, bb, gg);
+    if (RESUME) {  // resume at the boundary where the first launch stopped the shot
+        const TailRecord r = tc.rec[rec];
+        leg = r.leg;
+        sols = r.sols;
+        have = r.have != 0;
+        iters = r.iters;
+        Wbest = r.Wbest;
+        const float *lr = tc.lam + (size_t)rec * g.N;
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int j = threadIdx.x + q * NT;
+            if (j < g.N) Lam[q] = lr[j];
+        }
+        if (have)  // the kept solution, for the same-solution test
+            for (int q = tid; q < g.cor_words; q += NT) {
+                const uint64_t v = cor[q];
+                fb[2 * q] = (uint32_t)v;
+                fb[2 * q + 1] = (uint32_t)(v >> 32);
+            }
+    }
+    leg_init<MT, NT, VPT, DV, SKIP>(g, p, leg, msg, ws, Lam, bb, gg);
     __syncthreads();
     for (;;) {
         uint32_t *pc = par + pb * g.m_words;
@@ -82,6 +107,17 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
             t = 0;
             leg_init<MT, NT, VPT, DV, SKIP>(g, p, leg, msg, ws, Lam, bb, gg);
         }
+        // a long shot with a next leg to run is suspended if a record is free (the next
+        // leg's initialisation is redone on resumption from the same state); thread 0
+        // decides and takes the record, *s_slot tells the block (-1: go on)
+        if (!RESUME && tid == 0) {
+            int k = -1;
+            if (!done && tc.mode == 1 && iters >= tc.cut) {
+                const unsigned int c = atomicAdd(tc.count, 1u);
+                if (c < (unsigned int)tc.cap) k = (int)c;
+            }
+            *s_slot = k;
+        }
         __syncthreads();  // the weight and the next leg's initial messages are visible
         if (fresh) {
             const long long W = wacc[ab];
@@ -93,7 +129,19 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
             if (tid == 0) wacc[ab ^ 1] = 0;
             ab ^= 1;
         }
+        if (!RESUME && *s_slot >= 0) break;
         if (done) break;
+    }
+    const int slot = RESUME ? -1 : *s_slot;  // this shot's last leg end set it
+    if (slot >= 0) {  // suspended: the state at this boundary; the next leg runs on resumption
+        float *lr = tc.lam + (size_t)slot * g.N;
+#pragma unroll
+        for (int q = 0; q < VPT; ++q) {
+            const int j = threadIdx.x + q * NT;
+            if (j < g.N) lr[j] = Lam[q];
+        }
+        if (tid == 0) tc.rec[slot] = TailRecord{shot, leg, sols, have ? 1 : 0, iters, Wbest};
+        return;
     }
     if (!have) store_bits<NT>(cor, fw, g.cor_words);
     if (tid == 0) {
@@ -105,17 +153,19 @@ __device__ __forceinline__ void decode_shot(const FusedGraph &g, const DevParams
 
 // One block per shot at a time; shots come from a global counter (through the shot
 // map's index list when it has one).
-template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
+// RESUME: the second launch of the tail continuation; shots come from the records of the
+// first launch (counter then numbers the records taken).
+template <typename MT, int NT, int VPT, int MINB, int DC, int DV, bool RESUME = false>
 __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams p,
                                                    const uint64_t *__restrict__ syn, int B,
                                                    DecodeOut out, unsigned int *counter,
-                                                   ShotMap map) {
+                                                   ShotMap map, TailCont tc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *msg = smem_raw;
     uint32_t *fw, *fb, *sg, *par;
     float *ws;
     smem_layout(g, smem_raw, fw, fb, sg, par, ws);
-    __shared__ int s_shot;
+    __shared__ int s_shot, s_rec, s_slot;
     __shared__ long long s_wacc[2];
     block_setup<MT, NT, DC>(g, msg, fw, ws, p.clip);
 
@@ -125,19 +175,28 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode(FusedGraph g, DevParams
     int ab = 0;
     if (threadIdx.x < 2) s_wacc[threadIdx.x] = 0;
 
-    const int limit = map.order ? min(*map.count, B) : B;
+    const int limit = RESUME ? (int)min(*tc.count, (unsigned int)tc.cap)
+                             : (map.order ? min(*map.count, B) : B);
     for (;;) {
         __syncthreads();  // the previous shot is done with shared memory and s_shot
         if (threadIdx.x == 0) {
             const int k = (int)atomicAdd(counter, 1u);
-            s_shot = k < limit ? (map.order ? map.order[k] : k) : -1;
+            if (RESUME) {
+                s_rec = k < limit ? k : -1;
+                s_shot = k < limit ? tc.rec[k].shot : -1;
+            } else {
+                s_rec = -1;
+                s_shot = k < limit ? (map.order ? map.order[k] : k) : -1;
+            }
         }
         __syncthreads();
         const int shot = s_shot;
         if (shot < 0) break;
-        decode_shot<MT, NT, VPT, DC, DV>(g, p, shot, syn + (size_t)shot * map.syn_stride,
+        decode_shot<MT, NT, VPT, DC, DV, false, RESUME>(g, p, shot,
+                                         syn + (size_t)shot * map.syn_stride,
                                          out.corr + (size_t)shot * map.cor_stride, out, msg, fw,
-                                         fb, sg, par, ws, s_wacc, Lam, bb, gg, ab);
+                                         fb, sg, par, ws, s_wacc, Lam, bb, gg, ab, tc, s_rec,
+                                         &s_slot);
     }
 }
 
@@ -154,7 +213,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode_multi(MultiTable tab,
     unsigned char *msg = smem_raw;
     __shared__ FusedGraph s_g;
     __shared__ DevParams s_p;
-    __shared__ int s_shot, s_code;
+    __shared__ int s_shot, s_code, s_slot;
     __shared__ long long s_wacc[2];
     int cur = -1;
 
@@ -198,7 +257,8 @@ __global__ void __launch_bounds__(NT, MINB) fused_decode_multi(MultiTable tab,
         }
         decode_shot<MT, NT, VPT, DC, DV, true>(s_g, s_p, shot, syn + (size_t)shot * syn_stride,
                                          out.corr + (size_t)shot * cor_stride, out, msg, fw, fb,
-                                         sg, par, ws, s_wacc, Lam, bb, gg, ab);
+                                         sg, par, ws, s_wacc, Lam, bb, gg, ab, TailCont{},
+                                         -1, &s_slot);
     }
 }
 
@@ -251,12 +311,12 @@ __global__ void __launch_bounds__(NT) fused_trace(FusedGraph g, DevParams p,
     }
 }
 
-template <typename MT, int NT, int VPT, int MINB, int DC, int DV>
+template <typename MT, int NT, int VPT, int MINB, int DC, int DV, bool RESUME>
 cudaError_t launch_decode(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                           const DevParams &p, const uint64_t *syn, int B, DecodeOut out,
-                          unsigned int *counter, ShotMap map) {
-    fused_decode<MT, NT, VPT, MINB, DC, DV><<<grid, NT, smem, st>>>(g, p, syn, B, out, counter,
-                                                                    map);
+                          unsigned int *counter, ShotMap map, TailCont tc) {
+    fused_decode<MT, NT, VPT, MINB, DC, DV, RESUME><<<grid, NT, smem, st>>>(g, p, syn, B, out,
+                                                                            counter, map, tc);
     return cudaGetLastError();
 }
 
@@ -293,7 +353,14 @@ FusedKernel entry() {
     k.dc = QL_DC;
     k.dv = QL_DV;
     k.decode_fn = (const void *)fused_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
-    k.launch_decode = &launch_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
+    k.launch_decode = &launch_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV, false>;
+    if constexpr (NT == 1024) {  // the shapes of the tail continuation's second launch
+        k.resume_fn = (const void *)fused_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV, true>;
+        k.launch_resume = &launch_decode<MsgT, NT, VPT, MINB, QL_DC, QL_DV, true>;
+    } else {
+        k.resume_fn = nullptr;
+        k.launch_resume = nullptr;
+    }
     k.multi_fn = (const void *)fused_decode_multi<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
     k.launch_multi = &launch_multi<MsgT, NT, VPT, MINB, QL_DC, QL_DV>;
     if constexpr (TRACE) {
@@ -319,7 +386,8 @@ FusedKernel entry() {
 void QL_EXPAND(QL_P, QL_DC, QL_DV)(const FusedKernel **out, int *n) {
     // (threads, faults per thread, min resident blocks): the first entry whose
     // threads * vpt >= N is used unless the caller asks for a block size; the last
-    // entry also serves the trace kernel.
+    // entry also serves the trace kernel; the 1024-thread entries serve the resuming
+    // launch of the tail continuation.
     static const FusedKernel table[] = {
         entry<256, 4, 4, false>(),
         entry<512, 6, 2, false>(),
@@ -327,6 +395,7 @@ void QL_EXPAND(QL_P, QL_DC, QL_DV)(const FusedKernel **out, int *n) {
         entry<384, 8, 3, false>(),
         entry<640, 5, 2, false>(),
         entry<768, 4, 2, false>(),
+        entry<1024, 3, 1, false>(),
         entry<1024, 8, 1, false>(),
         entry<512, 16, 1, false>(),
         entry<512, 32, 1, true>(),

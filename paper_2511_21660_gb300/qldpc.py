@@ -61,6 +61,7 @@ class qldpc_relay_params(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("llr_clip", ctypes.c_float),
         ("gamma_table", ctypes.c_void_p),
+        ("tail_cut_iters", ctypes.c_int32),
     ]
 
 
@@ -79,7 +80,8 @@ class qldpc_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "M", "N", "E", "max_check_degree", "max_fault_degree", "kernel", "msg_precision",
         "block_threads", "blocks_per_sm", "num_sms", "grid_blocks", "smem_bytes",
-        "syndrome_words", "correction_words")]
+        "syndrome_words", "correction_words", "tail_cut_iters", "tail_block_threads",
+        "tail_records")]
 
 
 class QldpcError(RuntimeError):
@@ -309,6 +311,7 @@ class RelayConfig:
     kernel: int = QLDPC_KERNEL_AUTO
     block_threads: int = 0
     llr_clip: float = 0.0
+    tail_cut_iters: int = 0   # 0: T_1 + 8 T_r; < 0: no tail continuation
 
 
 class RelayDecoder:
@@ -328,7 +331,8 @@ class RelayDecoder:
         prm = qldpc_relay_params(cfg.legs_after_first, cfg.iters_first, cfg.iters_later,
                                  cfg.max_total_iters, cfg.stop_after_solutions,
                                  cfg.warm_start_mode, cfg.msg_precision, cfg.kernel,
-                                 cfg.block_threads, cfg.llr_clip, gam.ctypes.data)
+                                 cfg.block_threads, cfg.llr_clip, gam.ctypes.data,
+                                 cfg.tail_cut_iters)
         self.device = device
         self.handle = qldpc_create(self.M, self.N, row_ptr, col_idx, priors, prm, device)
         self.info = qldpc_get_info(self.handle)
