@@ -445,9 +445,13 @@ def post_processing_variants(args, dev, stream, flush, block_threads=0):
     first = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam[:1],
                          RelayConfig(legs_after_first=0, stop_after_solutions=1,
                                      block_threads=block_threads), device=dev.index)
-    relay = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam,
-                         RelayConfig(stop_after_solutions=S_SOLUTIONS,
-                                     block_threads=block_threads), device=dev.index)
+    # full Relay: the tail continuation on or off, whichever is faster on this batch
+    from paper_2511_21660_gb300.autotune import tune
+    rcfg = RelayConfig(stop_after_solutions=S_SOLUTIONS, block_threads=block_threads)
+    (_, tail), tail_ms = tune(P.row_ptr, P.col_idx, P.p, gam, rcfg, syn, repeats=1, cache=None,
+                              block_sizes=(block_threads,), tail_options=(0, -1))
+    rcfg.tail_cut_iters = tail
+    relay = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam, rcfg, device=dev.index)
     osd = FilteredOSD(P.row_ptr, P.col_idx, P.p, 25, conf, rmax, device=dev.index)
     accept, erase = -0.5, 4.5
     cluster = ClusterDecoder(P.row_ptr, P.col_idx, P.p, 25, accept, erase, 4096, 512,
@@ -490,6 +494,9 @@ def post_processing_variants(args, dev, stream, flush, block_threads=0):
            "mean_candidates": float(ncand[skip == 0].float().mean().item()) if todo else 0.0,
            "ler_first_leg_plus_osd": fail_first / n, "ler_relay_S5": fail_relay / n,
            "relay_ms": ms_relay,
+           "relay_tail_continuation": {"cut_iterations": relay.info.tail_cut_iters,
+                                       "resume_block_threads": relay.info.tail_block_threads,
+                                       "ms_by_block_and_cut": tail_ms},
            "relay_iterations_per_shot": {"mean": float(it_relay.double().mean().item()),
                                          "p99": float(torch.quantile(it_relay.double(), 0.99)),
                                          "max": int(it_relay.max().item()),
