@@ -675,6 +675,31 @@ def mixed_batch_variant(args, dev, stream, flush):
             "separate_total_ms": sum(v["ms"] for v in alone.values())}
 
 
+# Special-function (MUFU) operations per edge per iteration of the float32 soft kernels:
+# forward tanh(nu/2) = 1 - 2/(1 + e^nu) (exponential, reciprocal) and
+# atanh(P) = log((1+P)/(1-P))/2 (reciprocal, logarithm); the adjoint recomputes the
+# forward (4) and per reverse step evaluates tanh (2), atanh (2) and one reciprocal for
+# 1/(1 - P^2).
+SOFT_XU_OPS_FORWARD = 4
+SOFT_XU_OPS_BACKWARD = 4 + 5
+
+
+def soft_roofline(edge_iters, ms, ops_per_edge_iter, sms):
+    """The soft kernels' special-function roof: one warp-instruction per clock per SM on
+    the XU pipe (32 results/clock/SM; ncu's XU utilisation of the forward, 10.9% at 24.8M
+    XU warp-instructions over 1.50M active cycles per SM, gives the same peak) at the
+    maximum SM clock."""
+    mhz = sm_max_mhz()
+    peak = 32 * sms * mhz * 1e6
+    ops = ops_per_edge_iter * edge_iters / (ms / 1e3)
+    return {"bound": "xu", "achieved": ops / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+            "frac": ops / peak,
+            "peak_kind": "derived: 32 special-function results/clk/SM x %d SMs x %.0f MHz"
+                         % (sms, mhz),
+            "algorithmic": f"{ops_per_edge_iter} special-function operations per edge per "
+                           f"iteration x {edge_iters} edge-iterations"}
+
+
 def soft_dmem_variant(args, dev, stream, flush, B=4096):
     """One training step of the differentiable leg: unrolled soft DMem-BP (25 iterations,
     trainable gamma_j and alpha_t, BCE loss, checkpoints every 5 iterations, float32) on
@@ -707,11 +732,14 @@ def soft_dmem_variant(args, dev, stream, flush, B=4096):
             fwd.append(e[0].elapsed_time(e[1]))
             bwd.append(e[1].elapsed_time(e[2]))
     f_ms, b_ms = sum(fwd) / len(fwd), sum(bwd) / len(bwd)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     out = {"workload": f"gross T=12 p=0.003, batch {B}, 25 iterations, checkpoint every 5, "
                        "float32, gamma_j (2736) and alpha_t (25) trainable",
            "forward_ms": f_ms, "backward_ms": b_ms,
            "step_shots_per_s": B / ((f_ms + b_ms) / 1e3),
            "forward_edge_iterations_per_s": B * T * P.E / (f_ms / 1e3),
+           "roofline": soft_roofline(P.E * T * B, f_ms, SOFT_XU_OPS_FORWARD, sms),
+           "backward_roofline": soft_roofline(P.E * T * B, b_ms, SOFT_XU_OPS_BACKWARD, sms),
            "loss": float(loss.item()),
            "grad_gamma_norm": float(gg.norm().item())}
     if args.cpu_baseline:

@@ -146,3 +146,14 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
     assert "-O3" in r["build"] and "-ffp-contract=off" in r["build"]
     one = r["single_thread"]
     assert one["cores"] == 1 and one["value"] > 0 and one["edge_updates_per_s"] > 0
+
+
+def test_soft_roofline_counts_special_function_operations():
+    """4 (forward) and 9 (adjoint) special-function operations per edge-iteration against
+    32 results per clock per SM: batch 4096, E = 7344, 25 iterations in 2.78 ms."""
+    ei = 7344 * 25 * 4096
+    r = bench.soft_roofline(ei, 2.78, bench.SOFT_XU_OPS_FORWARD, 152)
+    peak = 32 * 152 * bench.sm_max_mhz() * 1e6
+    assert r["bound"] == "xu" and r["peak"] == pytest.approx(peak / 1e12)
+    assert r["frac"] == pytest.approx(4 * ei / 2.78e-3 / peak)
+    assert bench.SOFT_XU_OPS_BACKWARD == 9

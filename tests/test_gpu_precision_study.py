@@ -24,6 +24,7 @@ from workloads.torch_sampling import pack_bits_t, sample_faults_t, syndromes_t  
 
 N_GPU = 1_000_000
 N_ORACLE = 20_000
+N_MESSAGES = 256   # shots whose first 10 iterations are compared message by message
 
 
 def _two_sample_ok(f1, n1, f2, n2):
@@ -82,17 +83,19 @@ def test_logical_error_rate_and_message_error_by_precision(p, seed):
     # with the FP64 oracle, checked above on the oracle's shots)
     ok, *_ = _two_sample_ok(int(fails["fp16"].sum()), N_GPU, int(fails["fp32"].sum()), N_GPU)
     line["fp16_vs_fp32_within_2sigma_on_all_shots"] = bool(ok)
-    # messages of the first 10 iterations of the first leg, 32 shots
-    L64, nu64, _ = dmem_trace(P.row_ptr, P.col_idx, P.p, gam[0], s_host[:32], 10)
+    # messages of the first 10 iterations of the first leg, N_MESSAGES shots
     for name, prec, clip in (("fp16", QLDPC_MSG_FP16, 65504.0), ("fp32", QLDPC_MSG_FP32, 1e30)):
-        if name == "fp16":
-            L64, nu64, _ = dmem_trace(P.row_ptr, P.col_idx, P.p, gam[0], s_host[:32], 10, clip=clip)
+        L64, nu64, _ = dmem_trace(P.row_ptr, P.col_idx, P.p, gam[0], s_host[:N_MESSAGES], 10,
+                                  clip=clip)
         dec = RelayDecoder(P.row_ptr, P.col_idx, P.p, gam, RelayConfig(msg_precision=prec))
-        marg, nu, _ = dec.trace_first_leg(syn[:32].contiguous(), 10)
+        marg, nu, _ = dec.trace_first_leg(syn[:N_MESSAGES].contiguous(), 10)
         torch.cuda.synchronize()
         dec.close()
         nu = nu.cpu().numpy().transpose(1, 0, 2)
         err = np.abs(nu - nu64) / np.maximum(1.0, np.abs(nu64))
         line[f"max_message_error_{name}_t10"] = float(err.max())
+        line[f"p999_message_error_{name}_t10"] = float(np.quantile(err, 0.999))
+        del nu, nu64, err
+    line["message_error_shots"] = N_MESSAGES
     assert line["max_message_error_fp32_t10"] <= 1e-4
     print("PRECISION_STUDY " + json.dumps(line))
