@@ -677,11 +677,20 @@ def mixed_batch_variant(args, dev, stream, flush):
 
 # Special-function (MUFU) operations per edge per iteration of the float32 soft kernels:
 # forward tanh(nu/2) = 1 - 2/(1 + e^nu) (exponential, reciprocal) and
-# atanh(P) = log((1+P)/(1-P))/2 (reciprocal, logarithm); the adjoint recomputes the
-# forward (4) and per reverse step evaluates tanh (2), atanh (2) and one reciprocal for
-# 1/(1 - P^2).
+# atanh(P) = log((1+P)/(1-P))/2 (reciprocal, logarithm); per reverse step the adjoint
+# evaluates tanh (2), atanh (2) and one reciprocal for 1/(1 - P^2), and it recomputes
+# the forward (4) of every iteration but the last of each checkpoint segment other than
+# the final one.
 SOFT_XU_OPS_FORWARD = 4
-SOFT_XU_OPS_BACKWARD = 4 + 5
+SOFT_XU_OPS_REVERSE = 5
+
+
+def soft_backward_ops_per_edge_iter(T, K):
+    """Special-function operations per edge per iteration of the adjoint, averaged over
+    the T iterations (checkpoints every K): 5 T reverse plus 4 (T - ceil(T/K) + 1)
+    recomputed."""
+    nck = (T + K - 1) // K
+    return (SOFT_XU_OPS_REVERSE * T + SOFT_XU_OPS_FORWARD * (T - nck + 1)) / T
 
 
 def soft_roofline(edge_iters, ms, ops_per_edge_iter, sms):
@@ -696,7 +705,7 @@ def soft_roofline(edge_iters, ms, ops_per_edge_iter, sms):
             "frac": ops / peak,
             "peak_kind": "derived: 32 special-function results/clk/SM x %d SMs x %.0f MHz"
                          % (sms, mhz),
-            "algorithmic": f"{ops_per_edge_iter} special-function operations per edge per "
+            "algorithmic": f"{ops_per_edge_iter:.3g} special-function operations per edge per "
                            f"iteration x {edge_iters} edge-iterations"}
 
 
@@ -739,7 +748,8 @@ def soft_dmem_variant(args, dev, stream, flush, B=4096):
            "step_shots_per_s": B / ((f_ms + b_ms) / 1e3),
            "forward_edge_iterations_per_s": B * T * P.E / (f_ms / 1e3),
            "roofline": soft_roofline(P.E * T * B, f_ms, SOFT_XU_OPS_FORWARD, sms),
-           "backward_roofline": soft_roofline(P.E * T * B, b_ms, SOFT_XU_OPS_BACKWARD, sms),
+           "backward_roofline": soft_roofline(P.E * T * B, b_ms,
+                                              soft_backward_ops_per_edge_iter(T, 5), sms),
            "loss": float(loss.item()),
            "grad_gamma_norm": float(gg.norm().item())}
     if args.cpu_baseline:

@@ -14,7 +14,9 @@
 // shared memory and stores them every K iterations (checkpoints).  The adjoint
 // walks the checkpoint segments backwards: it recomputes the segment's forward from
 // its checkpoint, keeping each iteration's nu(t-1), Lambda(t-1) in a global
-// segment buffer, then runs the reverse iterations.  Per-shot gradients are summed
+// segment buffer, then runs the reverse iterations.  Only the last segment runs its
+// final iteration again (for Lambda(T)); in the others the recompute stops one
+// iteration short, and the state it ends on is the first reverse step's input.  Per-shot gradients are summed
 // over shots in a fixed order, so results are deterministic.
 #include "qldpc_internal.h"
 
@@ -253,24 +255,30 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
 
     for (int s = a.nck - 1; s >= 0; --s) {
         const int t0 = s * a.K, t1 = min(a.T_it, t0 + a.K);
+        const bool last = s == a.nck - 1;
         const T *ck = a.ckpt + ((size_t)b * a.nck + s) * EN;
         for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nu[e] = ck[e];
         for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) Lam[j] = ck[g.E + j];
         __syncthreads();
-        for (int t = t0 + 1; t <= t1; ++t) {
+        // states before iterations t0+1 .. t1; iteration t1 itself runs only in the last
+        // segment, whose Lambda(T) seeds the adjoint; elsewhere the state before t1 stays
+        // in shared memory for the first reverse step
+        for (int t = t0 + 1; t <= (last ? t1 : t1 - 1); ++t) {
             copy_state(nu, Lam, segb + (size_t)(t - t0 - 1) * EN, g.E, g.N);
             soft_iteration<T, DCM>(a, sy, t, nu, Lam);
         }
-        if (s == a.nck - 1) {  // Lambda(T) is in Lam: adjoint of the loss sum
+        if (last) {  // Lambda(T) is in Lam: adjoint of the loss sum
             for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS)
                 Lb[j] = RM<T>::sigmoid(Lam[j]) - (bit_of(fy, j) ? T(0) : T(1));
             for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nb[e] = 0;
         }
         __syncthreads();
         for (int t = t1; t > t0; --t) {
-            // the state before iteration t, staged in the forward arrays (free here)
-            copy_state(segb + (size_t)(t - t0 - 1) * EN, segb + (size_t)(t - t0 - 1) * EN + g.E,
-                       nu, g.E, g.N);
+            // the state before iteration t, staged in the forward arrays (free here; it is
+            // already there for the first reverse step of a segment that is not the last)
+            if (t < t1 || last)
+                copy_state(segb + (size_t)(t - t0 - 1) * EN,
+                           segb + (size_t)(t - t0 - 1) * EN + g.E, nu, g.E, g.N);
             __syncthreads();
             const T *nu_prev = nu;
             const T *L_prev = Lam;
