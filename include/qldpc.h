@@ -296,8 +296,8 @@ typedef struct {
 #define QLDPC_OSD_TOO_MANY (-1)    /* |R| > max_candidates; corrections[b] untouched          */
 #define QLDPC_OSD_NO_SOLUTION (-2) /* H_R x = sigma has no solution; corrections[b] untouched */
 
-/* Copy H (CSR as in qldpc_create, N <= 32767, check degree <= 32, fault degree <= 8)
- * and the priors to `device`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
+/* Copy H (CSR as in qldpc_create, M <= 32767, N <= 32767, check degree <= 32, fault
+ * degree <= 8) and the priors to `device`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM. */
 int qldpc_osd_create(qldpc_osd **out, int32_t M, int32_t N, const int32_t *row_ptr,
                      const int32_t *col_idx, const double *priors,
                      const qldpc_osd_params *params, int device);

@@ -14,9 +14,10 @@
 //   4. update loop (Sec. 6.4-6.7): the first invalid cluster c is grown by every
 //      neighbour of its vertices, every cluster the grown set meets is merged into c
 //      (and leaves the invalid list), the interior faults of c are found, and c is
-//      tested by the streaming GF(2) solver of one warp (gf2_warp.cuh) on its checks
-//      (rows, increasing index) and interior faults (columns, increasing index); an
-//      invalid c goes to the end of the list;
+//      tested by the GF(2) solver of one warp (gf2_warp.cuh) on its checks (rows,
+//      increasing index) and interior faults (columns, increasing index): dense
+//      elimination when the system fits the solver's region, else the streaming
+//      solver; an invalid c goes to the end of the list;
 //   5. output (Sec. 6.8): each surviving cluster's solution with free columns 0; the
 //      correction is F_pre + the union of those.
 //
@@ -79,35 +80,49 @@ __device__ __forceinline__ bool interior_of(const FusedGraph &g, const int16_t *
     return true;
 }
 
-// Streams the rows of cluster `lab` (its checks, increasing index) into the warp's
-// solver; columns are the cluster's interior faults (bitmap intr, word prefix wpre).
-// Returns false when the system has no solution.  Called by warp 0.
+// Solves the system of cluster `lab` (rows: its checks, increasing index; columns: its
+// interior faults, bitmap intr with word prefix wpre) by one warp, streaming the rows
+// (gf2_warp.cuh).  Returns consistency; with `want_x`, lane l's word of the solution
+// (free columns 0) goes to *x.
 template <int DC>
-__device__ __forceinline__ bool stream_cluster_rows(const FusedGraph &g, const ClusterArgs &a,
-                                                    const int16_t *label, int lab,
-                                                    const uint32_t *intr, const uint32_t *wpre,
-                                                    const uint32_t *sp, uint32_t &lockw,
-                                                    uint32_t &specw, uint32_t *up, int ncols) {
+__device__ __forceinline__ bool solve_cluster(const FusedGraph &g, const ClusterArgs &a,
+                                              const ClusterLayout &L, unsigned char *smem,
+                                              const int16_t *label, int lab,
+                                              const uint32_t *intr, const uint32_t *wpre,
+                                              const uint32_t *sp, int ncols, bool want_x,
+                                              uint32_t *x) {
     const int lane = threadIdx.x & 31;
-    for (int base = 0; base < g.M; base += 32) {
-        const int i = base + lane;
-        uint32_t bal = __ballot_sync(FULL, i < g.M && label[i] == lab);
-        while (bal) {
-            const int ci = base + __ffs(bal) - 1;
-            bal &= bal - 1u;
-            int pr = -1;
-            if (lane < DC) {
-                const int jv = __ldg(a.chk_var + (size_t)ci * DC + lane);
-                if (jv >= 0 && get_bit(intr, jv))
-                    pr = (int)wpre[jv >> 5] +
-                         __popc(intr[jv >> 5] & ((1u << (jv & 31)) - 1u));
-            }
-            const uint32_t row = gf2::row_from_positions(pr, DC);
-            const uint32_t spec = (sp[ci >> 5] >> (ci & 31)) & 1u;
-            if (!gf2::insert_row(row, spec, lockw, specw, up, a.W, ncols)) return false;
-        }
+    uint32_t *up = reinterpret_cast<uint32_t *>(smem + L.up);
+    int16_t *rows = reinterpret_cast<int16_t *>(smem + L.rows);
+    // the cluster's checks: lane l lists those of the contiguous range [i0, i1)
+    const int ch = (g.M + 31) / 32, i0 = min(g.M, lane * ch), i1 = min(g.M, i0 + ch);
+    int local = 0;
+    for (int i = i0; i < i1; ++i) local += label[i] == lab;
+    int incl = local;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += t;
     }
-    return true;
+    const int R = __shfl_sync(FULL, incl, 31);
+    int r = incl - local;
+    for (int i = i0; i < i1; ++i)
+        if (label[i] == lab) rows[r++] = (int16_t)i;
+    __syncwarp();
+    __shared__ uint32_t s_lk[32], s_sw[32];
+    uint32_t lockw, specw;
+    const bool ok = gf2::solve_stream<DC>(
+        R, ncols, up, s_lk, s_sw, lockw, specw,
+        [&](int rr, int k) {
+            const int jv = __ldg(a.chk_var + (size_t)rows[rr] * DC + k);
+            if (jv < 0 || !get_bit(intr, jv)) return -1;
+            return (int)wpre[jv >> 5] + __popc(intr[jv >> 5] & ((1u << (jv & 31)) - 1u));
+        },
+        [&](int rr) {
+            const int c = rows[rr];
+            return (sp[c >> 5] >> (c & 31)) & 1u;
+        });
+    if (want_x) *x = ok ? gf2::back_substitute(lockw, specw, up, (ncols + 31) >> 5, ncols) : 0u;
+    return ok;
 }
 
 // Two blocks per SM where the kernel fits in 64 registers without spilling (8 faults
@@ -132,7 +147,6 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
     uint32_t *spre = reinterpret_cast<uint32_t *>(smem_raw + L.spre);
     uint8_t *mflag = smem_raw + L.flags;
     int16_t *queue = reinterpret_cast<int16_t *>(smem_raw + L.queue);
-    uint32_t *up = reinterpret_cast<uint32_t *>(smem_raw + L.up);
     uint32_t *fw = reinterpret_cast<uint32_t *>(smem_raw + cluster_union_bytes(g, a));
     uint32_t *fb = fw + g.f_words;
     uint32_t *sg = fb + g.f_words;
@@ -145,11 +159,11 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
     const int NWp = 2 * g.cor_words;  // fault bitmaps padded to whole 64-bit words
     const int MW = g.m_words, KC = a.max_clusters;
 
-    float Lam[VPT], bb[VPT], gg[VPT];
-#pragma unroll
-    for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
-
     for (;;) {
+        // per-shot registers, declared here so that nothing of them lives across shots
+        float Lam[VPT], bb[VPT], gg[VPT];
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
         __syncthreads();  // the previous shot is done with shared memory
         if (tid == 0) s_shot = (int)atomicAdd(counter, 1u);
         __syncthreads();
@@ -318,9 +332,8 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
             }
             // validity of c by warp 0
             if (warp == 0) {
-                uint32_t lockw = 0u, specw = 0u;
-                const bool ok = stream_cluster_rows<DC>(g, a, label, c, intr, wpre, sp, lockw,
-                                                        specw, up, n);
+                const bool ok = solve_cluster<DC>(g, a, L, smem_raw, label, c, intr, wpre, sp, n,
+                                                  false, nullptr);
                 if (lane == 0) s_valid = ok;
             }
             __syncthreads();
@@ -354,9 +367,9 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
             __syncthreads();
             if (warp == 0) {
                 const int n = warp_word_prefix(intr, wpre, NWp);
-                uint32_t lockw = 0u, specw = 0u;
-                stream_cluster_rows<DC>(g, a, label, id, intr, wpre, sp, lockw, specw, up, n);
-                s_x[lane] = gf2::back_substitute(lockw, specw, up, a.W, n);
+                uint32_t xw = 0u;
+                solve_cluster<DC>(g, a, L, smem_raw, label, id, intr, wpre, sp, n, true, &xw);
+                s_x[lane] = xw;
             }
             __syncthreads();
             for (int j = tid; j < g.N; j += NT) {

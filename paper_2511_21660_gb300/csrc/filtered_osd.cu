@@ -14,12 +14,12 @@
 //      systolic solver applies it; gf2_warp.cuh): one warp streams the touched rows in
 //      check order; a row is reduced by locked pivot rows until its leftmost 1 (in
 //      ranking order) is an unlocked column, where it is stored with its syndrome bit;
-//      a row reduced to zero with syndrome bit 1 means no solution.  Back substitution
-//      over the locked columns, from the right, gives x with free columns 0;
+//      a row reduced to zero with syndrome bit 1 means no solution.  Several rows are
+//      reduced at a time (one per lane, or one per lane group for wide rows).  Back
+//      substitution over the locked columns, from the right, gives x with free columns 0;
 //   5. F_j = x_r for j = R_r (Sec. 5, "Algorithm output").
 //
-// A pivot row is a W-word bitset over ranking positions held by lanes 0..W-1 (lane l
-// owns word l), so the reduction of a row by a pivot row is one 32-bit XOR per lane.
+// A row is a bitset over ranking positions, 32 columns per word.
 #include "gf2_warp.cuh"
 #include "relay_device.cuh"
 
@@ -62,24 +62,25 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
                                                     OsdOut out, unsigned int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *msg = smem_raw;
-    uint64_t *keys = reinterpret_cast<uint64_t *>(smem_raw);
-    uint32_t *up = reinterpret_cast<uint32_t *>(smem_raw + 8 * (size_t)o.KP);
-    int16_t *pos = reinterpret_cast<int16_t *>(smem_raw + 8 * (size_t)o.KP +
-                                               4 * (size_t)o.max_cand * o.W);
+    const OsdLayout L = osd_layout(g, o);
+    int16_t *pos = reinterpret_cast<int16_t *>(smem_raw + L.pos);
+    uint64_t *keys = reinterpret_cast<uint64_t *>(smem_raw + L.region);
+    uint32_t *up = reinterpret_cast<uint32_t *>(smem_raw + L.region);  // after the sort
+    int16_t *rows = reinterpret_cast<int16_t *>(smem_raw + L.rows);
     uint32_t *fw = reinterpret_cast<uint32_t *>(smem_raw + osd_union_bytes(g, o));
     uint32_t *fb = fw + g.f_words;
     uint32_t *sg = fb + g.f_words;
     uint32_t *par = sg + 2 * g.syn_words;
     float *ws = reinterpret_cast<float *>(par + 2 * g.m_words);
     __shared__ int s_shot, s_cnt, s_bad;
-    __shared__ uint32_t s_x[32];
+    __shared__ uint32_t s_x[32], s_lk[32], s_sw[32];
     const int tid = threadIdx.x, lane = tid & 31;
 
-    float Lam[VPT], bb[VPT], gg[VPT];
-#pragma unroll
-    for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
-
     for (;;) {
+        // per-shot registers, declared here so that nothing of them lives across shots
+        float Lam[VPT], bb[VPT], gg[VPT];
+#pragma unroll
+        for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
         __syncthreads();  // the previous shot is done with shared memory
         if (tid == 0) s_shot = (int)atomicAdd(counter, 1u);
         __syncthreads();
@@ -153,29 +154,37 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
             if (sg[q] & ~par[q]) s_bad = 1;  // a syndrome bit on a row H_R leaves empty
         __syncthreads();
 
-        // 4. lifted elimination and back substitution by warp 0
+        // 4. elimination by warp 0
         if (tid < 32 && !s_bad) {
-            uint32_t lockw = 0u, specw = 0u;  // lane l: locked / syndrome bits of word l
-            bool bad = false;
-            for (int w = 0; w < g.m_words && !bad; ++w) {
-                uint32_t tw = par[w];
-                while (tw) {
-                    const int c = 32 * w + __ffs(tw) - 1;
-                    tw &= tw - 1u;
-                    int pr = -1;
-                    if (lane < DC) {
-                        const int jv = __ldg(o.chk_var + (size_t)c * DC + lane);
-                        if (jv >= 0) pr = pos[jv];
-                    }
-                    const uint32_t row = gf2::row_from_positions(pr, DC);
-                    const uint32_t spec = (sg[c >> 5] >> (c & 31)) & 1u;
-                    if (!gf2::insert_row(row, spec, lockw, specw, up, o.W, n)) {
-                        bad = true;
-                        break;
-                    }
-                }
+            // the touched checks in increasing index: lane l lists those of a contiguous
+            // chunk of bitmap words
+            const int ch = (g.m_words + 31) / 32, w0 = min(g.m_words, lane * ch);
+            const int w1 = min(g.m_words, w0 + ch);
+            int local = 0;
+            for (int w = w0; w < w1; ++w) local += __popc(par[w]);
+            int incl = local;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(FULL, incl, d);
+                if (lane >= d) incl += t;
             }
-            const uint32_t xw = bad ? 0u : gf2::back_substitute(lockw, specw, up, o.W, n);
+            const int R = __shfl_sync(FULL, incl, 31);
+            int r = incl - local;
+            for (int w = w0; w < w1; ++w)
+                for (uint32_t tw = par[w]; tw; tw &= tw - 1u) rows[r++] = (int16_t)(32 * w + __ffs(tw) - 1);
+            __syncwarp();
+            uint32_t lockw, specw;
+            const bool ok = gf2::solve_stream<DC>(
+                R, n, up, s_lk, s_sw, lockw, specw,
+                [&](int rr, int k) {
+                    const int jv = __ldg(o.chk_var + (size_t)rows[rr] * DC + k);
+                    return jv >= 0 ? (int)pos[jv] : -1;
+                },
+                [&](int rr) {
+                    const int c = rows[rr];
+                    return (sg[c >> 5] >> (c & 31)) & 1u;
+                });
+            const bool bad = !ok;
+            const uint32_t xw = ok ? gf2::back_substitute(lockw, specw, up, (n + 31) >> 5, n) : 0u;
             s_x[lane] = xw;
             if (lane == 0 && bad) s_bad = 1;
         }
@@ -191,11 +200,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
         }
         for (int q = tid; q < 2 * g.cor_words; q += NT) fw[q] = 0u;
         __syncthreads();
-        for (int r = tid; r < n; r += NT)
-            if ((s_x[r >> 5] >> (r & 31)) & 1u) {
-                const int j = (int)(uint32_t)keys[r];
-                atomicOr(fw + (j >> 5), 1u << (j & 31));
-            }
+        for (int j = tid; j < g.N; j += NT) {
+            const int r = pos[j];
+            if (r >= 0 && ((s_x[r >> 5] >> (r & 31)) & 1u)) atomicOr(fw + (j >> 5), 1u << (j & 31));
+        }
         __syncthreads();
         store_bits<NT>(out.corr + (size_t)shot * g.cor_words, fw, g.cor_words);
         if (tid == 0) {

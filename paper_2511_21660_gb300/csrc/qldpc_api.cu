@@ -1217,6 +1217,7 @@ int qldpc_osd_create(qldpc_osd **out, int32_t M, int32_t N, const int32_t *row_p
     int rc = validate_graph(M, N, row_ptr, col_idx, priors);
     if (rc) return rc;
     if (N > 32767) return fail(QLDPC_ERR_UNSUPPORTED, "N = %d above 32767", N);
+    if (M > 32767) return fail(QLDPC_ERR_UNSUPPORTED, "M = %d above 32767", M);
 
     qldpc_osd *o = new (std::nothrow) qldpc_osd();
     if (!o) return fail(QLDPC_ERR_OOM, "host allocation failed");

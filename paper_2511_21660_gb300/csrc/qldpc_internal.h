@@ -163,13 +163,27 @@ struct OsdKernel {
                           const uint8_t *skip, int B, OsdOut out, unsigned int *counter);
 };
 void osd_table(const OsdKernel **out, int *n);
-// The OSD stage reuses the message area: keys [KP] u64, pivot rows [max_cand][W] u32,
-// the inverse ranking [N] i16.
+// The OSD stage reuses the message area: the inverse ranking [N] i16, then one region
+// that holds the sort keys [KP] u64 and, once the inverse ranking is built, the pivot
+// rows [max_cand][W] u32, then the list of touched checks [M] i16.
+struct OsdLayout {
+    size_t pos, region, region_bytes, rows, total;
+};
+__host__ __device__ inline OsdLayout osd_layout(const FusedGraph &g, const OsdArgs &o) {
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t keys = 8 * (size_t)o.KP, rows = 4 * (size_t)o.max_cand * o.W;
+    OsdLayout L;
+    size_t x = 0;
+    L.pos = x;    x = al(x + 2 * (size_t)g.N);
+    L.region = x; L.region_bytes = al(keys > rows ? keys : rows); x += L.region_bytes;
+    L.rows = x;   x = al(x + 2 * (size_t)g.M);
+    L.total = x;
+    return L;
+}
 __host__ __device__ inline size_t osd_union_bytes(const FusedGraph &g, const OsdArgs &o) {
     const size_t msg = ((size_t)g.msg_bytes + 15) & ~(size_t)15;
-    const size_t osd = 8 * (size_t)o.KP + 4 * (size_t)o.max_cand * o.W + 2 * (size_t)g.N;
-    const size_t u = msg > osd ? msg : osd;
-    return (u + 15) & ~(size_t)15;
+    const size_t osd = osd_layout(g, o).total;
+    return msg > osd ? msg : osd;
 }
 inline size_t osd_smem_bytes(const FusedGraph &g, const OsdArgs &o) {
     return osd_union_bytes(g, o) + 8 * (size_t)g.f_words + 8 * (size_t)g.syn_words +
@@ -205,9 +219,10 @@ struct ClusterKernel {
 void cluster_table(const ClusterKernel **out, int *n);
 // The cluster stage reuses the message area: labels [M+N] i16, the grown-vertex bitmap,
 // interior / partial-correction / erasure / correction bitmaps over faults, their word
-// prefix counts, the updated syndrome, per-cluster flags and queue, pivot rows.
+// prefix counts, the updated syndrome, per-cluster flags and queue, pivot rows, the
+// list of the cluster's checks [M] i16.
 struct ClusterLayout {
-    size_t label, grown, intr, wpre, fpre, fera, fout, sp, spre, flags, queue, up, total;
+    size_t label, grown, intr, wpre, fpre, fera, fout, sp, spre, flags, queue, up, rows, total;
 };
 __host__ __device__ inline ClusterLayout cluster_layout(const FusedGraph &g, const ClusterArgs &a) {
     auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
@@ -228,6 +243,7 @@ __host__ __device__ inline ClusterLayout cluster_layout(const FusedGraph &g, con
     L.flags = o; o = al(o + 2 * (size_t)a.max_clusters);   // merge flag, alive flag
     L.queue = o; o = al(o + 2 * (size_t)a.max_clusters);
     L.up = o;    o = al(o + 4 * (size_t)a.max_cols * a.W);
+    L.rows = o;  o = al(o + 2 * (size_t)g.M);
     L.total = o;
     return L;
 }
