@@ -14,8 +14,8 @@
 // word per lane (lane l: columns 32 l .. 32 l + 31).
 //
 // Several rows are in flight at once.  The stored rows do not change while rows are
-// reduced; the reduced rows are then stored one by one, and a row whose leading column
-// another row has just taken goes back for more reduction.  Every stored row still has a
+// reduced; then, for each free column that reduced rows lead with, one of them is stored,
+// and the others go back for more reduction.  Every stored row still has a
 // leading column of its own, so the stored rows are an echelon basis of the rows seen, as
 // with one row at a time.  The pivot columns (the leading positions of any echelon basis
 // of the span), the inconsistency (a row in the span of the stored rows with the other
@@ -55,9 +55,9 @@ __device__ __forceinline__ uint32_t back_substitute(uint32_t lockw, uint32_t spe
 
 // One row per lane (ceil(ncols / 32) <= NWR).  Rounds: every lane with a row reduces it
 // until it is 0 or its leading 1 is a free column; zero rows retire (right-hand side 1:
-// no solution); the other rows are stored in lane order, unless an earlier lane took
-// their leading column in this round; lanes whose row was stored or retired take the next
-// rows of the stream.  lk and sw are 32-word shared arrays for the pivot bitmaps.
+// no solution); of the other rows, the lowest lane's row for each leading column is
+// stored; lanes whose row was stored or retired take the next rows of the stream.  lk and
+// sw are 32-word shared arrays for the pivot bitmaps.
 template <int DC, int NWR, typename RowPos, typename RowSpec>
 __device__ __forceinline__ bool stream_rows_lanes(int R, int ncols, uint32_t *up, int stride,
                                                   uint32_t *lk, uint32_t *sw, uint32_t &lockw,
@@ -72,15 +72,15 @@ __device__ __forceinline__ bool stream_rows_lanes(int R, int ncols, uint32_t *up
     bool fresh = true, ok = true;
     uint32_t r[NWR];
     uint32_t spec = 0u;
-    // every round stores or retires at least one row (the first lane with a nonzero row
-    // finds its leading column still free), so R + 1 rounds suffice
+    // every round stores or retires at least one row (each leading column met is free
+    // and one row per such column is stored), so R + 1 rounds suffice
     for (int round = 0; round <= R; ++round) {
         if (fresh) {
 #pragma unroll
             for (int q = 0; q < NWR; ++q) r[q] = 0u;
             spec = 0u;
             if (cur >= 0) {
-#pragma unroll
+#pragma unroll 8
                 for (int k = 0; k < DC; ++k) {
                     const int p = rowpos(cur, k);
                     const uint32_t bit = p >= 0 ? 1u << (p & 31) : 0u;
@@ -125,24 +125,21 @@ __device__ __forceinline__ bool stream_rows_lanes(int R, int ncols, uint32_t *up
             ok = false;
             break;
         }
-        unsigned retired = __ballot_sync(kFull, zero);
-        for (unsigned pend = active & ~retired; pend; pend &= pend - 1u) {
-            const int h = __ffs(pend) - 1;
-            const int lh = __shfl_sync(kFull, lead, h);
-            const uint32_t sh = __shfl_sync(kFull, spec, h);
-            const int w = lh >> 5, b = lh & 31;
-            if ((lk[w] >> b) & 1u) continue;  // taken in this round: reduce again
-            if (lane == h) {
-                uint32_t *pr = up + (size_t)lh * stride;
+        // store: of the rows that share a leading column, the lowest lane's (the others
+        // reduce again by it next round); rows with distinct leading columns are stored
+        // side by side
+        const bool pend = cur >= 0 && lead >= 0;
+        const unsigned same = __match_any_sync(kFull, pend ? lead : -1 - lane);
+        const bool store = pend && (same & ((1u << lane) - 1u)) == 0u;
+        if (store) {
+            uint32_t *pr = up + (size_t)lead * stride;
 #pragma unroll
-                for (int q = 0; q < NWR; ++q)
-                    if (q < nw) pr[q] = r[q];
-                lk[w] |= 1u << b;
-                sw[w] |= sh << b;
-            }
-            __syncwarp();
-            retired |= 1u << h;
+            for (int q = 0; q < NWR; ++q)
+                if (q < nw) pr[q] = r[q];
+            atomicOr(lk + (lead >> 5), 1u << (lead & 31));
+            if (spec) atomicOr(sw + (lead >> 5), 1u << (lead & 31));
         }
+        const unsigned retired = __ballot_sync(kFull, zero || store);
         if ((retired >> lane) & 1u) {
             const int k = __popc(retired & ((1u << lane) - 1u));
             cur = next + k < R ? next + k : -1;
