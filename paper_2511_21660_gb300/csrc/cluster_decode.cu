@@ -82,8 +82,8 @@ __device__ __forceinline__ bool interior_of(const FusedGraph &g, const int16_t *
 
 // Solves the system of cluster `lab` (rows: its checks, increasing index; columns: its
 // interior faults, bitmap intr with word prefix wpre) by one warp, streaming the rows
-// (gf2_warp.cuh).  Returns consistency; with `want_x`, lane l's word of the solution
-// (free columns 0) goes to *x.
+// (gf2_warp.cuh); lab < 0 takes the checks of every cluster.  Returns consistency; with
+// `want_x`, lane l's word of the solution (free columns 0) goes to *x.
 template <int DC>
 __device__ __forceinline__ bool solve_cluster(const FusedGraph &g, const ClusterArgs &a,
                                               const ClusterLayout &L, unsigned char *smem,
@@ -97,7 +97,8 @@ __device__ __forceinline__ bool solve_cluster(const FusedGraph &g, const Cluster
     // the cluster's checks: lane l lists those of the contiguous range [i0, i1)
     const int ch = (g.M + 31) / 32, i0 = min(g.M, lane * ch), i1 = min(g.M, i0 + ch);
     int local = 0;
-    for (int i = i0; i < i1; ++i) local += label[i] == lab;
+    auto member = [&](int i) { return lab < 0 ? label[i] >= 0 : label[i] == lab; };
+    for (int i = i0; i < i1; ++i) local += member(i);
     int incl = local;
     for (int d = 1; d < 32; d <<= 1) {
         const int t = __shfl_up_sync(FULL, incl, d);
@@ -106,7 +107,7 @@ __device__ __forceinline__ bool solve_cluster(const FusedGraph &g, const Cluster
     const int R = __shfl_sync(FULL, incl, 31);
     int r = incl - local;
     for (int i = i0; i < i1; ++i)
-        if (label[i] == lab) rows[r++] = (int16_t)i;
+        if (member(i)) rows[r++] = (int16_t)i;
     __syncwarp();
     __shared__ uint32_t s_lk[32], s_sw[32];
     uint32_t lockw, specw;
@@ -351,14 +352,46 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
             continue;
         }
 
-        // 5. solutions of the clusters that own an interior fault
-        for (int q = tid; q < NWp; q += NT) fout[q] = 0u;
+        // 5. solutions of the clusters that own an interior fault.  The clusters are
+        // disjoint and the checks of an interior fault all lie in its cluster, so the
+        // clusters' systems are the diagonal blocks of one system (rows: the checks of
+        // every cluster; columns: every interior fault).  A column is independent of the
+        // columns left of it exactly when it is so within its block, so the pivot columns
+        // are the blocks' together and the solution with free columns 0 is the blocks'
+        // side by side: one solve serves every cluster when the interior faults fit the
+        // solver's width; otherwise the clusters are solved one by one.
+        for (int q = tid; q < NWp; q += NT) fout[q] = intr[q] = 0u;
+        __syncthreads();
         for (int j = tid; j < g.N; j += NT) {
             const int lab = label[g.M + j];
-            if (lab >= 0 && interior_of<DV>(g, label, j, lab)) mflag[lab] = 1;
+            if (lab >= 0 && interior_of<DV>(g, label, j, lab)) {
+                mflag[lab] = 1;
+                set_bit(intr, j);
+            }
         }
         __syncthreads();
-        for (int id = 0; id < ns + ne; ++id) {
+        if (warp == 0) {
+            const int n = warp_word_prefix(intr, wpre, NWp);
+            if (lane == 0) s_nint = n;
+        }
+        __syncthreads();
+        const bool joint = s_nint <= a.max_cols;
+        if (joint) {
+            if (warp == 0) {
+                uint32_t xw = 0u;
+                solve_cluster<DC>(g, a, L, smem_raw, label, -1, intr, wpre, sp, s_nint, true,
+                                  &xw);
+                s_x[lane] = xw;
+            }
+            __syncthreads();
+            for (int j = tid; j < g.N; j += NT) {
+                if (!get_bit(intr, j)) continue;
+                const int pc = (int)wpre[j >> 5] + __popc(intr[j >> 5] & ((1u << (j & 31)) - 1u));
+                if ((s_x[pc >> 5] >> (pc & 31)) & 1u) set_bit(fout, j);
+            }
+            __syncthreads();
+        }
+        for (int id = 0; id < (joint ? 0 : ns + ne); ++id) {
             if (!mflag[id]) continue;  // uniform: every thread reads the same flag
             for (int q = tid; q < NWp; q += NT) intr[q] = 0u;
             __syncthreads();

@@ -7,6 +7,10 @@
   streamed, pivots locked at their leftmost 1, then back substitution) written out
   here independently gives the same solution on larger random systems, with the rows
   in any order;
+* the same elimination with several rows in flight (the kernels' scheme: each round
+  reduces every row in flight by the stored rows, then stores, for each free leading
+  column met, the row of the lowest slot, the others going back for more reduction)
+  reaches the same solution and the same verdict with 1, 4 or 32 slots;
 * the ranking: strict threshold, increasing LLR, ties by fault index (the broadcast
   insertion sorter keeps equal keys in arrival order, and the LLRs arrive by index);
 * the pipeline on a detector model: every OSD correction satisfies its syndrome and is
@@ -109,6 +113,72 @@ def test_streaming_elimination_reaches_the_same_solution(seed):
     x, ok, _ = gf2_solve_leftmost(A, y)
     for order in (np.arange(m), rng.permutation(m)):
         z = _lifted_gauss_jordan(A[order], y[order])
+        assert (z is not None) == ok
+        if ok:
+            assert (z == x).all()
+
+
+def _rounds_of_rows(A, y, slots):
+    """Rows taken from the stream by `slots` slots; per round every slot's row is reduced
+    by the stored rows (which stay fixed during the round) until it is 0 or leads with a
+    free column; a zero row with right-hand side 1 means no solution; for each free
+    leading column, the row of the lowest slot leading with it is stored; slots whose row
+    was stored or was 0 take the next rows.  Then back substitution."""
+    m, n = A.shape
+    up = np.zeros((n, n), dtype=np.uint8)
+    spec = np.zeros(n, dtype=np.uint8)
+    locked = np.zeros(n, dtype=bool)
+    cur = [k if k < m else -1 for k in range(slots)]
+    rows = [A[k].copy() if k < m else None for k in range(slots)]
+    rhs = [int(y[k]) if k < m else 0 for k in range(slots)]
+    nxt = slots
+    while any(c >= 0 for c in cur):
+        lead = [-1] * slots
+        for k in range(slots):
+            if cur[k] < 0:
+                continue
+            while rows[k].any():
+                p = int(np.argmax(rows[k]))
+                lead[k] = p
+                if not locked[p]:
+                    break
+                rows[k] ^= up[p]
+                rhs[k] ^= int(spec[p])
+            else:
+                lead[k] = -1
+        done = []
+        for k in range(slots):
+            if cur[k] >= 0 and lead[k] < 0:
+                if rhs[k]:
+                    return None
+                done.append(k)
+        for k in range(slots):
+            if cur[k] >= 0 and lead[k] >= 0 and lead[k] not in lead[:k]:
+                up[lead[k]], spec[lead[k]], locked[lead[k]] = rows[k], rhs[k], True
+                done.append(k)
+        for k in sorted(done):
+            cur[k] = nxt if nxt < m else -1
+            if cur[k] >= 0:
+                rows[k], rhs[k] = A[nxt].copy(), int(y[nxt])
+            nxt += 1
+    x = np.zeros(n, dtype=np.uint8)
+    for p in range(n - 1, -1, -1):
+        if locked[p]:
+            x[p] = (spec[p] + int((up[p, p + 1:] & x[p + 1:]).sum())) % 2
+    return x
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_rows_in_flight_reach_the_same_solution(seed):
+    rng = np.random.default_rng(300 + seed)
+    m, n = int(rng.integers(20, 120)), int(rng.integers(10, 90))
+    A = (rng.random((m, n)) < 0.06).astype(np.uint8)
+    y = (A.astype(int) @ (rng.random(n) < 0.2)) % 2
+    if seed % 4 == 3:
+        y[int(rng.integers(0, m))] ^= 1                # usually inconsistent
+    x, ok, _ = gf2_solve_leftmost(A, y)
+    for slots in (1, 4, 32):
+        z = _rounds_of_rows(A, y, slots)
         assert (z is not None) == ok
         if ok:
             assert (z == x).all()
