@@ -277,7 +277,9 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
             __syncthreads();
             const int c = s_c;
             if (c < 0) break;
-            // grow: every vertex of c and its neighbours
+            // grow: every vertex of c and its neighbours; a neighbour in another cluster
+            // flags that cluster for merging (labels do not change in this pass)
+            for (int q = tid; q < NWp; q += NT) intr[q] = 0u;
             for (int v = tid; v < V; v += NT) {
                 if (label[v] != c) continue;
                 set_bit(grown, v);
@@ -285,38 +287,46 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
                     for (int k = 0; k < DC; ++k) {
                         const int jv = __ldg(a.chk_var + (size_t)v * DC + k);
                         if (jv < 0) break;
+                        const int lu = label[g.M + jv];
                         set_bit(grown, g.M + jv);
+                        if (lu >= 0 && lu != c) mflag[lu] = 1;
                     }
                 } else {
                     const int j = v - g.M, deg = fault_degree<DV>(g, j);
-                    for (int k = 0; k < deg; ++k)
-                        set_bit(grown, __ldg(g.var_chk + (size_t)j * DV + k));
+                    for (int k = 0; k < deg; ++k) {
+                        const int u = __ldg(g.var_chk + (size_t)j * DV + k);
+                        const int lu = label[u];
+                        set_bit(grown, u);
+                        if (lu >= 0 && lu != c) mflag[lu] = 1;
+                    }
                 }
             }
             __syncthreads();
-            // merge: the clusters the grown set meets
-            for (int v = tid; v < V; v += NT) {
-                const int lab = label[v];
-                if (lab >= 0 && lab != c && get_bit(grown, v)) mflag[lab] = 1;
-            }
-            __syncthreads();
+            // merge: the grown set and the flagged clusters join c
             for (int v = tid; v < V; v += NT) {
                 const int lab = label[v];
                 if (get_bit(grown, v) || (lab >= 0 && mflag[lab])) label[v] = (int16_t)c;
             }
-            if (tid == 0) {  // merged clusters leave the invalid list
-                int k = 0;
-                for (int q = 0; q < s_count; ++q) {
-                    const int at = (s_head + q) % KC;
-                    const int id = queue[at];
-                    if (!mflag[id]) queue[(s_head + k++) % KC] = (int16_t)id;
+            if (warp == NT / 32 - 1) {  // merged clusters leave the invalid list, in order
+                const int cnt = s_count, head = s_head;
+                int kept = 0;
+                for (int q0 = 0; q0 < cnt; q0 += 32) {
+                    const int q = q0 + lane;
+                    const int at = head + q >= KC ? head + q - KC : head + q;
+                    const int id = q < cnt ? queue[at] : 0;
+                    const bool keep = q < cnt && !mflag[id];
+                    const unsigned bal = __ballot_sync(FULL, keep);
+                    if (keep) {
+                        const int to = head + kept + __popc(bal & ((1u << lane) - 1u));
+                        queue[to >= KC ? to - KC : to] = (int16_t)id;
+                    }
+                    kept += __popc(bal);
+                    __syncwarp();
                 }
-                s_count = k;
+                if (lane == 0) s_count = kept;
             }
             __syncthreads();
-            for (int q = tid; q < ns + ne; q += NT) mflag[q] = 0;
-            for (int q = tid; q < NWp; q += NT) intr[q] = 0u;
-            __syncthreads();
+            for (int q = tid; q < ns + ne; q += NT) mflag[q] = 0;  // next read after two barriers
             // interior faults of c
             for (int j = tid; j < g.N; j += NT)
                 if (interior_of<DV>(g, label, j, c)) set_bit(intr, j);
