@@ -98,7 +98,19 @@ __device__ __forceinline__ bool solve_cluster(const FusedGraph &g, const Cluster
     const int ch = (g.M + 31) / 32, i0 = min(g.M, lane * ch), i1 = min(g.M, i0 + ch);
     int local = 0;
     auto member = [&](int i) { return lab < 0 ? label[i] >= 0 : label[i] == lab; };
-    for (int i = i0; i < i1; ++i) local += member(i);
+    bool odd = false;  // a row with syndrome bit 1
+    for (int i = i0; i < i1; ++i)
+        if (member(i)) {
+            ++local;
+            odd |= (sp[i >> 5] >> (i & 31)) & 1u;
+        }
+    // no syndrome bit: x = 0 solves it (and is the solution with free columns 0); no
+    // column: only the zero syndrome is in the image
+    const bool any_odd = __any_sync(FULL, odd);
+    if (!any_odd || ncols == 0) {
+        if (want_x) *x = 0u;
+        return !any_odd;
+    }
     int incl = local;
     for (int d = 1; d < 32; d <<= 1) {
         const int t = __shfl_up_sync(FULL, incl, d);
