@@ -306,7 +306,10 @@ int qldpc_osd_create(qldpc_osd **out, int32_t M, int32_t N, const int32_t *row_p
  * or NULL (post-process every shot); corrections [B][ceil(N/64)] u64, written only for
  * solved shots (pass the pre-decoder's corrections to keep them elsewhere); status [B]
  * int32 (QLDPC_OSD_*); n_candidates [B] int32 |R| or NULL.  Asynchronous on `stream`
- * (cudaStream_t, NULL = legacy default stream).  Errors: INVALID_ARG, CUDA. */
+ * (cudaStream_t, NULL = legacy default stream), except that with a skip mask the handle
+ * lists the shots to post-process in a device array of B entries, allocated on the first
+ * such call and whenever B grows (the call then waits for the device).  One call at a
+ * time per handle.  Errors: INVALID_ARG, CUDA. */
 int qldpc_osd_decode_batch(qldpc_osd *o, const uint64_t *syndromes, int64_t B,
                            const uint8_t *skip, uint64_t *corrections, int32_t *status,
                            int32_t *n_candidates, void *stream);
@@ -356,7 +359,9 @@ int qldpc_cluster_create(qldpc_cluster **out, int32_t M, int32_t N, const int32_
 
 /* Decode B shots (device pointers): syndromes [B][ceil(M/64)] u64; skip [B] u8 or NULL;
  * corrections [B][ceil(N/64)] u64, written only for decoded shots; status [B] int32
- * (QLDPC_CLUSTER_*); steps [B] int32 growth steps or NULL.  Asynchronous on `stream`.
+ * (QLDPC_CLUSTER_*); steps [B] int32 growth steps or NULL.  Asynchronous on `stream`,
+ * with the same list of shots as qldpc_osd_decode_batch when skip is given (allocated on
+ * the first such call and whenever B grows).  One call at a time per handle.
  * Errors: INVALID_ARG, CUDA. */
 int qldpc_cluster_decode_batch(qldpc_cluster *c, const uint64_t *syndromes, int64_t B,
                                const uint8_t *skip, uint64_t *corrections, int32_t *status,

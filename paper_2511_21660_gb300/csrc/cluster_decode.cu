@@ -144,7 +144,7 @@ __device__ __forceinline__ bool solve_cluster(const FusedGraph &g, const Cluster
 template <int NT, int VPT, int DC, int DV>
 __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_decode(FusedGraph g, DevParams p, ClusterArgs a,
                                                         const uint64_t *__restrict__ syn,
-                                                        const uint8_t *__restrict__ skip, int B,
+                                                        const int32_t *__restrict__ list, int B,
                                                         ClusterOut out, unsigned int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *msg = smem_raw;
@@ -167,6 +167,8 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
     float *ws = reinterpret_cast<float *>(par + 2 * g.m_words);
     __shared__ int s_shot, s_ns, s_ne, s_status, s_c, s_head, s_count, s_steps, s_nint, s_valid;
     __shared__ uint32_t s_x[32];
+    // the shots: list[0 .. counter[1]) (the host's compaction of a skip mask), else 0 .. B-1
+    const int n_work = list ? (int)counter[1] : B;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int V = g.M + g.N, VW = (V + 31) / 32, NW = (g.N + 31) / 32;
     const int NWp = 2 * g.cor_words;  // fault bitmaps padded to whole 64-bit words
@@ -180,15 +182,8 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
         __syncthreads();  // the previous shot is done with shared memory
         if (tid == 0) s_shot = (int)atomicAdd(counter, 1u);
         __syncthreads();
-        const int shot = s_shot;
-        if (shot >= B) break;
-        if (skip && skip[shot]) {
-            if (tid == 0) {
-                out.status[shot] = 0;
-                if (out.steps) out.steps[shot] = 0;
-            }
-            continue;
-        }
+        if (s_shot >= n_work) break;
+        const int shot = list ? list[s_shot] : s_shot;
 
         // 1. plain BP
         if (tid == 0) {
@@ -448,8 +443,8 @@ __global__ void __launch_bounds__(NT, VPT <= 8 && DC <= 16 ? 2 : 1) cluster_deco
 template <int NT, int VPT, int DC, int DV>
 cudaError_t launch_cluster(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                            const DevParams &p, const ClusterArgs &a, const uint64_t *syn,
-                           const uint8_t *skip, int B, ClusterOut out, unsigned int *counter) {
-    cluster_decode<NT, VPT, DC, DV><<<grid, NT, smem, st>>>(g, p, a, syn, skip, B, out, counter);
+                           const int32_t *list, int B, ClusterOut out, unsigned int *counter) {
+    cluster_decode<NT, VPT, DC, DV><<<grid, NT, smem, st>>>(g, p, a, syn, list, B, out, counter);
     return cudaGetLastError();
 }
 

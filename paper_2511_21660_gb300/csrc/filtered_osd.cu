@@ -58,7 +58,7 @@ __device__ __forceinline__ void bitonic_sort(uint64_t *keys, int n) {
 template <int NT, int VPT, int DC, int DV>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 : 1)) osd_decode(FusedGraph g, DevParams p, OsdArgs o,
                                                     const uint64_t *__restrict__ syn,
-                                                    const uint8_t *__restrict__ skip, int B,
+                                                    const int32_t *__restrict__ list, int B,
                                                     OsdOut out, unsigned int *counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *msg = smem_raw;
@@ -73,6 +73,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
     uint32_t *par = sg + 2 * g.syn_words;
     float *ws = reinterpret_cast<float *>(par + 2 * g.m_words);
     __shared__ int s_shot, s_cnt, s_bad;
+    // the shots: list[0 .. counter[1]) (the host's compaction of a skip mask), else 0 .. B-1
+    const int n_work = list ? (int)counter[1] : B;
     __shared__ uint32_t s_x[32], s_lk[32], s_sw[32];
     const int tid = threadIdx.x, lane = tid & 31;
 
@@ -84,15 +86,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
         __syncthreads();  // the previous shot is done with shared memory
         if (tid == 0) s_shot = (int)atomicAdd(counter, 1u);
         __syncthreads();
-        const int shot = s_shot;
-        if (shot >= B) break;
-        if (skip && skip[shot]) {
-            if (tid == 0) {
-                out.status[shot] = 0;
-                if (out.ncand) out.ncand[shot] = 0;
-            }
-            continue;
-        }
+        if (s_shot >= n_work) break;
+        const int shot = list ? list[s_shot] : s_shot;
 
         // 1. plain BP: lambda_j(t) = w_j (gamma row of zeros), Lambda from the priors
         if (tid == 0) {
@@ -216,8 +211,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
 template <int NT, int VPT, int DC, int DV>
 cudaError_t launch_osd(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                        const DevParams &p, const OsdArgs &o, const uint64_t *syn,
-                       const uint8_t *skip, int B, OsdOut out, unsigned int *counter) {
-    osd_decode<NT, VPT, DC, DV><<<grid, NT, smem, st>>>(g, p, o, syn, skip, B, out, counter);
+                       const int32_t *list, int B, OsdOut out, unsigned int *counter) {
+    osd_decode<NT, VPT, DC, DV><<<grid, NT, smem, st>>>(g, p, o, syn, list, B, out, counter);
     return cudaGetLastError();
 }
 

@@ -1188,13 +1188,67 @@ cudaError_t configure_kernel(const void *fn, int threads, size_t smem, int devic
 
 }  // namespace
 
+// The shots a post-processor is to take: the indices b with skip[b] == 0, in any order
+// (each shot's result depends on its own inputs only), appended to list by warp-wide
+// ballots; count ends as their number.  Skipped shots get their status (and the extra
+// per-shot output) 0 here, so the post-processor visits only the listed shots.
+__global__ void compact_active(const uint8_t *__restrict__ skip, int B, int32_t *list,
+                               unsigned int *count, int32_t *status, int32_t *extra) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = b < B && !skip[b];
+    if (b < B && !act) {
+        status[b] = 0;
+        if (extra) extra[b] = 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, act);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (act) list[base + __popc(m & ((1u << lane) - 1u))] = b;
+}
+
+// Post-processor work list: with a skip mask, the listed shots (the list grows with B on
+// the host, which then waits for the device); without one, every shot.  counter[0] is
+// the work counter, counter[1] the list's length.
+struct WorkList {
+    int32_t *list = nullptr;
+    int64_t cap = 0;
+};
+
+static cudaError_t prepare_work(WorkList &w, const uint8_t *skip, int64_t B, int32_t *status,
+                                int32_t *extra, unsigned int *counter, cudaStream_t st,
+                                const int32_t **list) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), st);
+    *list = nullptr;
+    if (e != cudaSuccess || !skip) return e;
+    if (B > w.cap) {
+        if (w.list) {
+            e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess) e = cudaFree(w.list);
+            w.list = nullptr;
+            w.cap = 0;
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaMalloc(&w.list, sizeof(int32_t) * (size_t)B);
+        if (e != cudaSuccess) return e;
+        w.cap = B;
+    }
+    compact_active<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(skip, (int)B, w.list, counter + 1,
+                                                               status, extra);
+    *list = w.list;
+    return cudaGetLastError();
+}
+
 struct qldpc_osd {
     int device = 0;
     qldpc_decoder *bp = nullptr;  // fused graph of H (float32 messages, gamma row of zeros)
     const OsdKernel *k = nullptr;
     OsdArgs args{};
-    void *arena = nullptr;        // chk_var and the work counter
+    void *arena = nullptr;        // chk_var and the work counters
     unsigned int *counter = nullptr;
+    WorkList work;
     size_t smem = 0;
     int grid = 0;
 };
@@ -1300,10 +1354,11 @@ int qldpc_osd_decode_batch(qldpc_osd *o, const uint64_t *syndromes, int64_t B,
         if (ptrs[q] && !is_device_ptr(ptrs[q]))
             return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    QL_CUDA(cudaMemsetAsync(o->counter, 0, sizeof(unsigned int), st));
+    const int32_t *list = nullptr;
+    QL_CUDA(prepare_work(o->work, skip, B, status, n_candidates, o->counter, st, &list));
     const int grid = (int)std::min<int64_t>(o->grid, B);
     QL_CUDA(o->k->launch(dim3(grid), o->smem, st, o->bp->fg, o->bp->prm, o->args, syndromes,
-                         skip, (int)B, OsdOut{corrections, status, n_candidates}, o->counter));
+                         list, (int)B, OsdOut{corrections, status, n_candidates}, o->counter));
     return QLDPC_OK;
 }
 
@@ -1312,6 +1367,7 @@ void qldpc_osd_destroy(qldpc_osd *o) {
     {
         DeviceGuard guard(o->device);
         if (o->arena) cudaFree(o->arena);  // waits for work that may still use it
+        if (o->work.list) cudaFree(o->work.list);
     }
     qldpc_destroy(o->bp);
     delete o;
@@ -1326,8 +1382,9 @@ struct qldpc_cluster {
     qldpc_decoder *bp = nullptr;  // fused graph of H (float32 messages, gamma row of zeros)
     const ClusterKernel *k = nullptr;
     ClusterArgs args{};
-    void *arena = nullptr;        // chk_var and the work counter
+    void *arena = nullptr;        // chk_var and the work counters
     unsigned int *counter = nullptr;
+    WorkList work;
     size_t smem = 0;
     int grid = 0;
 };
@@ -1434,10 +1491,11 @@ int qldpc_cluster_decode_batch(qldpc_cluster *o, const uint64_t *syndromes, int6
         if (ptrs[q] && !is_device_ptr(ptrs[q]))
             return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    QL_CUDA(cudaMemsetAsync(o->counter, 0, sizeof(unsigned int), st));
+    const int32_t *list = nullptr;
+    QL_CUDA(prepare_work(o->work, skip, B, status, steps, o->counter, st, &list));
     const int grid = (int)std::min<int64_t>(o->grid, B);
     QL_CUDA(o->k->launch(dim3(grid), o->smem, st, o->bp->fg, o->bp->prm, o->args, syndromes,
-                         skip, (int)B, ClusterOut{corrections, status, steps}, o->counter));
+                         list, (int)B, ClusterOut{corrections, status, steps}, o->counter));
     return QLDPC_OK;
 }
 
@@ -1446,6 +1504,7 @@ void qldpc_cluster_destroy(qldpc_cluster *o) {
     {
         DeviceGuard guard(o->device);
         if (o->arena) cudaFree(o->arena);  // waits for work that may still use it
+        if (o->work.list) cudaFree(o->work.list);
     }
     qldpc_destroy(o->bp);
     delete o;

@@ -160,7 +160,7 @@ struct OsdKernel {
     const void *fn;
     cudaError_t (*launch)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                           const DevParams &p, const OsdArgs &o, const uint64_t *syn,
-                          const uint8_t *skip, int B, OsdOut out, unsigned int *counter);
+                          const int32_t *list, int B, OsdOut out, unsigned int *counter);
 };
 void osd_table(const OsdKernel **out, int *n);
 // The OSD stage reuses the message area: the inverse ranking [N] i16, then one region
@@ -214,7 +214,7 @@ struct ClusterKernel {
     const void *fn;
     cudaError_t (*launch)(dim3 grid, size_t smem, cudaStream_t st, const FusedGraph &g,
                           const DevParams &p, const ClusterArgs &a, const uint64_t *syn,
-                          const uint8_t *skip, int B, ClusterOut out, unsigned int *counter);
+                          const int32_t *list, int B, ClusterOut out, unsigned int *counter);
 };
 void cluster_table(const ClusterKernel **out, int *n);
 // The cluster stage reuses the message area: labels [M+N] i16, the grown-vertex bitmap,
