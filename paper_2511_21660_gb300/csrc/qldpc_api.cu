@@ -926,7 +926,7 @@ struct qldpc_soft {
 namespace {
 
 size_t soft_workspace_layout(const qldpc_soft *s, int64_t B, size_t off[6]) {
-    const size_t rs = s->fp64 ? 8 : 4, EN = (size_t)s->E + s->N;
+    const size_t rs = s->fp64 ? 8 : 4, EN = (size_t)s->g.E + s->N;  // edge slots + faults
     const int nck = (s->T + s->K - 1) / s->K;
     const size_t sz[6] = {(size_t)B * nck * EN * rs, (size_t)B * s->K * EN * rs, (size_t)B * rs,
                           (size_t)B * s->N * rs, (size_t)B * s->T * rs, (size_t)B * s->N * rs};
@@ -1014,17 +1014,31 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
     s->K = checkpoint_every;
     s->fp64 = real_type == QLDPC_REAL_FP64;
     s->eps = s->fp64 ? 1e-15 : 1.1920928955078125e-07;  // |product| <= 1 - eps
-    std::vector<int32_t> var_ptr(N + 1, 0), var_edges(std::max(s->E, 1)), fill(N, 0);
     for (int i = 0; i < M; ++i) s->dc_max = std::max(s->dc_max, row_ptr[i + 1] - row_ptr[i]);
+    // float32 rows of at most 8 edges are padded to 8 slots (row i: slots 8 i .. 8 i + 7),
+    // which the kernels read and write as 16-byte halves
+    const bool pad = !s->fp64 && s->dc_max <= 8;
+    const int slots = pad ? 8 * M : s->E;
+    std::vector<int32_t> rp(M + 1), deg(std::max(M, 1)), ci(std::max(slots, 1));
+    for (int i = 0; i < M; ++i) {
+        const int d = row_ptr[i + 1] - row_ptr[i];
+        rp[i] = pad ? 8 * i : row_ptr[i];
+        deg[i] = d;
+        for (int k = 0; k < (pad ? 8 : d); ++k)
+            ci[rp[i] + k] = col_idx[row_ptr[i] + (k < d ? k : 0)];
+    }
+    rp[M] = slots;
+    std::vector<int32_t> var_ptr(N + 1, 0), var_edges(std::max(slots, 1)), fill(N, 0);
     for (int e = 0; e < s->E; ++e) var_ptr[col_idx[e] + 1]++;
     for (int j = 0; j < N; ++j) {
         s->dv_max = std::max(s->dv_max, var_ptr[j + 1]);
         var_ptr[j + 1] += var_ptr[j];
     }
-    for (int e = 0; e < s->E; ++e) {
-        const int j = col_idx[e];
-        var_edges[var_ptr[j] + fill[j]++] = e;
-    }
+    for (int i = 0; i < M; ++i)
+        for (int k = 0; k < deg[i]; ++k) {
+            const int j = col_idx[row_ptr[i] + k];
+            var_edges[var_ptr[j] + fill[j]++] = rp[i] + k;
+        }
     auto cleanup = [&](int code) {
         std::string msg = g_last_error;
         qldpc_soft_destroy(s);
@@ -1037,7 +1051,7 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
     SoftGraph &g = s->g;
     g.M = M;
     g.N = N;
-    g.E = s->E;
+    g.E = slots;
     g.syn_words = (M + 63) / 64;
     g.cor_words = (N + 63) / 64;
     int optin = 0;
@@ -1047,11 +1061,11 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
         return cleanup(fail(QLDPC_ERR_UNSUPPORTED, "soft state needs %zu B of shared memory, above %d",
                             soft_smem_backward(g, s->T, s->fp64), optin));
     const size_t rs = s->fp64 ? 8 : 4;
-    const size_t sizes[5] = {sizeof(int32_t) * (M + 1), sizeof(int32_t) * std::max(s->E, 1),
-                             sizeof(int32_t) * (N + 1), sizeof(int32_t) * std::max(s->E, 1),
-                             rs * N};
-    size_t off[5], o = 0;
-    for (int q = 0; q < 5; ++q) {
+    const size_t sizes[6] = {sizeof(int32_t) * (M + 1), sizeof(int32_t) * std::max(slots, 1),
+                             sizeof(int32_t) * (N + 1), sizeof(int32_t) * std::max(slots, 1),
+                             rs * N, sizeof(int32_t) * std::max(M, 1)};
+    size_t off[6], o = 0;
+    for (int q = 0; q < 6; ++q) {
         off[q] = o;
         o = align_up(o + sizes[q], 256);
     }
@@ -1064,10 +1078,10 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
         w32[j] = (float)w64[j];
     }
     char *base = static_cast<char *>(s->arena);
-    const void *src[5] = {row_ptr, s->E > 0 ? (const void *)col_idx : (const void *)var_edges.data(),
-                          var_ptr.data(), var_edges.data(),
-                          s->fp64 ? (const void *)w64.data() : (const void *)w32.data()};
-    for (int q = 0; q < 5; ++q) {
+    const void *src[6] = {rp.data(), ci.data(), var_ptr.data(), var_edges.data(),
+                          s->fp64 ? (const void *)w64.data() : (const void *)w32.data(),
+                          deg.data()};
+    for (int q = 0; q < 6; ++q) {
         e = cudaMemcpy(base + off[q], src[q], sizes[q], cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cleanup(fail(QLDPC_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e)));
     }
@@ -1075,6 +1089,7 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
     g.col_idx = reinterpret_cast<const int32_t *>(base + off[1]);
     g.var_ptr = reinterpret_cast<const int32_t *>(base + off[2]);
     g.var_edges = reinterpret_cast<const int32_t *>(base + off[3]);
+    g.row_deg = pad ? reinterpret_cast<const int32_t *>(base + off[5]) : nullptr;
     s->w = base + off[4];
     *out = s;
     return QLDPC_OK;

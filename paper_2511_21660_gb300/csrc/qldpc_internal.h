@@ -278,12 +278,13 @@ cudaError_t launch_baseline(int B, int threads, size_t smem, cudaStream_t st, co
 
 // CSR / CSC graph of the soft kernels (device pointers).
 struct SoftGraph {
-    int M, N, E;
+    int M, N, E;               // E: edge slots (8 M when the rows are padded)
     int syn_words, cor_words;
-    const int32_t *row_ptr;    // [M+1]
-    const int32_t *col_idx;    // [E]
+    const int32_t *row_ptr;    // [M+1] first slot of each row
+    const int32_t *row_deg;    // [M] row degrees when the rows are padded to 8 slots, else null
+    const int32_t *col_idx;    // [E] fault of each slot (padding slots: the row's first fault)
     const int32_t *var_ptr;    // [N+1]
-    const int32_t *var_edges;  // [E] edges of fault j in increasing edge order
+    const int32_t *var_edges;  // [E] slots of fault j in increasing slot order
 };
 
 // Everything one soft forward or backward launch needs (device pointers; real

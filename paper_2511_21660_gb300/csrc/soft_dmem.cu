@@ -97,14 +97,57 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
     return s;
 }
 
-// Check products of one row: P_k = prod_{l != k} tanh(nu_l/2), clamped.  The row
-// has d <= DCM edges.  float32 forms them from prefix and suffix products (O(d));
-// FP64 multiplies in increasing l, as the oracle does.
+// Rows of the edge arrays.  float32 with rows of at most 8 edges (the library pads
+// them: row i holds slots 8 i .. 8 i + 7, its degree in row_deg): two 16-byte halves,
+// read and written in an order that alternates with i / 4, so that the 8 lanes of a
+// quarter warp (8 consecutive rows) meet 32 distinct banks.  Otherwise the CSR row,
+// element by element.  Slots k >= d are read as 0 and not written.
 template <typename T, int DCM>
-__device__ __forceinline__ void row_products(const T *nu_row, int d, T eps, T (&tau)[DCM],
+__host__ __device__ constexpr bool padded_rows() { return sizeof(T) == 4 && DCM == 8; }
+
+template <typename T, int DCM>
+__device__ __forceinline__ void load_row(const T *row, int i, int d, T (&v)[DCM]) {
+    if constexpr (padded_rows<T, DCM>()) {
+        const bool h = (i >> 2) & 1;
+        const float4 a = reinterpret_cast<const float4 *>(row)[h ? 1 : 0];
+        const float4 b = reinterpret_cast<const float4 *>(row)[h ? 0 : 1];
+        const float4 lo = h ? b : a, hi = h ? a : b;
+        v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+        v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < DCM; ++k) v[k] = k < d ? row[k] : T(0);
+    }
+}
+
+template <typename T, int DCM>
+__device__ __forceinline__ void store_row(T *row, int i, int d, const T (&v)[DCM]) {
+    if constexpr (padded_rows<T, DCM>()) {
+        const bool h = (i >> 2) & 1;
+        const float4 lo = make_float4(v[0], v[1], v[2], v[3]);
+        const float4 hi = make_float4(v[4], v[5], v[6], v[7]);
+        reinterpret_cast<float4 *>(row)[h ? 1 : 0] = h ? hi : lo;
+        reinterpret_cast<float4 *>(row)[h ? 0 : 1] = h ? lo : hi;
+    } else {
+#pragma unroll
+        for (int k = 0; k < DCM; ++k)
+            if (k < d) row[k] = v[k];
+    }
+}
+
+__device__ __forceinline__ void row_span(const SoftGraph &g, int i, int &e0, int &d) {
+    e0 = g.row_ptr[i];
+    d = g.row_deg ? g.row_deg[i] : g.row_ptr[i + 1] - e0;
+}
+
+// Check products of one row: P_k = prod_{l != k} tanh(nu_l/2), clamped.  The row
+// has d <= DCM edges (values v).  float32 forms them from prefix and suffix products
+// (O(d)); FP64 multiplies in increasing l, as the oracle does.
+template <typename T, int DCM>
+__device__ __forceinline__ void row_products(const T (&v)[DCM], int d, T eps, T (&tau)[DCM],
                                              T (&P)[DCM], bool (&cl)[DCM]) {
 #pragma unroll
-    for (int k = 0; k < DCM; ++k) tau[k] = k < d ? RM<T>::tanh_half(nu_row[k]) : T(1);
+    for (int k = 0; k < DCM; ++k) tau[k] = k < d ? RM<T>::tanh_half(v[k]) : T(1);
     T suf[DCM];
     if constexpr (sizeof(T) == 4) {
         suf[DCM - 1] = T(1);
@@ -143,14 +186,16 @@ __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint6
     const SoftGraph &g = a.g;
     const T at = a.alpha[t - 1];
     for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
-        const int e0 = g.row_ptr[i], d = g.row_ptr[i + 1] - e0;
-        T tau[DCM], P[DCM];
+        int e0, d;
+        row_span(g, i, e0, d);
+        T v[DCM], tau[DCM], P[DCM];
         bool cl[DCM];
-        row_products<T, DCM>(nu + e0, d, a.eps, tau, P, cl);
+        load_row<T, DCM>(nu + e0, i, d, v);
+        row_products<T, DCM>(v, d, a.eps, tau, P, cl);
         const T s = bit_of(sy, i) ? T(-2) : T(2);
 #pragma unroll
-        for (int k = 0; k < DCM; ++k)
-            if (k < d) nu[e0 + k] = at * s * RM<T>::atanh_(P[k]);
+        for (int k = 0; k < DCM; ++k) v[k] = k < d ? at * s * RM<T>::atanh_(P[k]) : T(0);
+        store_row<T, DCM>(nu + e0, i, d, v);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
@@ -313,16 +358,19 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
             const T at = a.alpha[t - 1];
             T apart = 0;
             for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
-                const int e0 = g.row_ptr[i], d = g.row_ptr[i + 1] - e0;
-                T tau[DCM], P[DCM], Pb[DCM];
+                int e0, d;
+                row_span(g, i, e0, d);
+                T v[DCM], tau[DCM], P[DCM], Pb[DCM], mbv[DCM];
                 bool cl[DCM];
-                row_products<T, DCM>(nu_prev + e0, d, a.eps, tau, P, cl);
+                load_row<T, DCM>(nu_prev + e0, i, d, v);
+                row_products<T, DCM>(v, d, a.eps, tau, P, cl);
+                load_row<T, DCM>(nb + e0, i, d, mbv);
                 const T s2 = bit_of(sy, i) ? T(-2) : T(2);
 #pragma unroll
                 for (int k = 0; k < DCM; ++k) {
                     Pb[k] = 0;
                     if (k < d) {
-                        const T mb = nb[e0 + k];
+                        const T mb = mbv[k];
                         apart += mb * s2 * RM<T>::atanh_(P[k]);
                         if (!cl[k]) Pb[k] = RM<T>::div(mb * at * s2, T(1) - P[k] * P[k]);
                     }
@@ -348,11 +396,13 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
 #pragma unroll
                 for (int k = 0; k < DCM; ++k) {
                     if (k > 0) Y = Pb[k - 1] * pre[k - 1] + tau[k - 1] * Y;
+                    mbv[k] = T(0);
                     if (k < d) {
                         const T tb = pre[k] * X[k] + Y * suf[k];
-                        nb[e0 + k] = inner ? tb * (T(1) - tau[k] * tau[k]) / T(2) : T(0);
+                        mbv[k] = inner ? tb * (T(1) - tau[k] * tau[k]) / T(2) : T(0);
                     }
                 }
+                store_row<T, DCM>(nb + e0, i, d, mbv);
             }
             const T asum = block_sum(apart, red);  // includes the barrier
             if (threadIdx.x == 0) as[t - 1] += asum;
