@@ -186,3 +186,27 @@ def test_fp32_tracks_fp64_oracle_on_the_gross_code():
     assert np.abs(gg.cpu().numpy() - gg_ref).max() <= 1e-3 * np.abs(gg_ref).max()
     assert np.abs(ga.cpu().numpy() - ga_ref).max() <= 1e-3 * np.abs(ga_ref).max()
     soft.close()
+
+
+def test_fp32_tracks_fp64_oracle_on_a_14_round_gross_graph():
+    """Gross code, 14 rounds (1080 x 3168, more faults than 12 per thread): the float32
+    forward and adjoint against the FP64 oracle, with the 12-round graph's tolerances."""
+    P = phenomenological_dem(BB144, 14, 0.003)
+    F = sample_faults(P.p, 23, 8)
+    s = syndromes_of(P.row_ptr, P.col_idx, F)
+    rng = np.random.default_rng(23)
+    gam = rng.uniform(0.0, 0.3, P.N).astype(np.float32).astype(np.float64)
+    alpha = rng.uniform(0.25, 0.4, 25).astype(np.float32).astype(np.float64)
+    L_ref, gg_ref, ga_ref, m_ref = soft_dmem(P.row_ptr, P.col_idx, P.p, gam, alpha, s, F,
+                                             eps=EPS32, marginals=True)
+    soft = SoftDMem(P.row_ptr, P.col_idx, P.p, iterations=25, checkpoint_every=5)
+    syn, flt, g, a = _dev(P, F, s, gam, alpha, torch.float32)
+    loss, marg, ws = soft.forward(syn, flt, g, a, marginals=True)
+    gg, ga = soft.backward(syn, flt, g, a, ws)
+    torch.cuda.synchronize()
+    err = np.abs(marg.cpu().numpy() - m_ref) / np.maximum(1.0, np.abs(m_ref))
+    assert err.max() <= 1e-3, err.max()
+    assert abs(loss.item() - L_ref) <= 1e-4 * L_ref
+    assert np.abs(gg.cpu().numpy() - gg_ref).max() <= 1e-3 * np.abs(gg_ref).max()
+    assert np.abs(ga.cpu().numpy() - ga_ref).max() <= 1e-3 * np.abs(ga_ref).max()
+    soft.close()
