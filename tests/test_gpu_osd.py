@@ -73,6 +73,10 @@ def test_osd_matches_oracle_on_every_shot(code, T, p, n, conf, rmax):
     _assert_same(got, ref, f"{code.n} T={T}")
     st = got[1]
     assert (st == QLDPC_OSD_SOLVED).sum() >= n // 3
+    if rmax == 1024:  # every width of the eliminated rows: 8 or 16 words in registers, lane groups
+        nc = got[2]
+        for lo, hi in ((1, 256), (257, 512), (513, rmax)):
+            assert ((nc >= lo) & (nc <= hi)).any(), (lo, hi)
     ok = st == QLDPC_OSD_SOLVED
     assert (((got[0][ok].astype(np.int64) @ P.H.T.astype(np.int64)) % 2) == sig[ok]).all()
 
