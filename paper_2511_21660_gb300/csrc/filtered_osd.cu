@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
     uint32_t *sg = fb + g.f_words;
     uint32_t *par = sg + 2 * g.syn_words;
     float *ws = reinterpret_cast<float *>(par + 2 * g.m_words);
-    __shared__ int s_shot, s_cnt, s_bad;
+    __shared__ int s_shot, s_cnt, s_bad, s_rows;
     // the shots: list[0 .. counter[1]) (the host's compaction of a skip mask), else 0 .. B-1
     const int n_work = list ? (int)counter[1] : B;
     __shared__ uint32_t s_x[32], s_lk[32], s_sw[32];
@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
         if (tid == 0) {
             s_cnt = 0;
             s_bad = 0;
+            s_rows = 0;
         }
         plain_bp<NT, VPT, DC, DV>(g, p, o.bp_iters, syn + (size_t)shot * g.syn_words, msg, fw,
                                   sg, par, ws, Lam, bb, gg);
@@ -149,28 +150,35 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
             if (sg[q] & ~par[q]) s_bad = 1;  // a syndrome bit on a row H_R leaves empty
         __syncthreads();
 
-        // 4. elimination by warp 0
-        if (tid < 32 && !s_bad) {
-            // the touched checks in increasing index: lane l lists those of a contiguous
-            // chunk of bitmap words
-            const int ch = (g.m_words + 31) / 32, w0 = min(g.m_words, lane * ch);
-            const int w1 = min(g.m_words, w0 + ch);
-            int local = 0;
-            for (int w = w0; w < w1; ++w) local += __popc(par[w]);
-            int incl = local;
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(FULL, incl, d);
-                if (lane >= d) incl += t;
+        // 4. the touched checks (the rows of H_R), listed by the whole block in any order
+        // (the elimination's result does not depend on it), with each row's ranking
+        // positions in a table after the pivot rows' space when it fits there
+        const int nw = (n + 31) >> 5;
+        const size_t piv_words = ((size_t)n * nw + 3) & ~(size_t)3;
+        int16_t *tab = reinterpret_cast<int16_t *>(up + piv_words);
+        const int tab_rows = (int)((L.region_bytes - 4 * piv_words) / (2 * DC));
+        if (!s_bad)
+            for (int c = tid; c < g.M; c += NT) {
+                if (!((par[c >> 5] >> (c & 31)) & 1u)) continue;
+                const int r = atomicAdd(&s_rows, 1);
+                rows[r] = (int16_t)c;
+                if (r < tab_rows)
+                    for (int k = 0; k < DC; ++k) {
+                        const int jv = __ldg(o.chk_var + (size_t)c * DC + k);
+                        tab[r * DC + k] = jv >= 0 ? pos[jv] : (int16_t)-1;
+                    }
             }
-            const int R = __shfl_sync(FULL, incl, 31);
-            int r = incl - local;
-            for (int w = w0; w < w1; ++w)
-                for (uint32_t tw = par[w]; tw; tw &= tw - 1u) rows[r++] = (int16_t)(32 * w + __ffs(tw) - 1);
-            __syncwarp();
+        __syncthreads();
+
+        // 5. elimination by warp 0
+        if (tid < 32 && !s_bad) {
+            const int R = s_rows;
+            const bool in_tab = R <= tab_rows;
             uint32_t lockw, specw;
             const bool ok = gf2::solve_stream<DC>(
                 R, n, up, s_lk, s_sw, lockw, specw,
                 [&](int rr, int k) {
+                    if (in_tab) return (int)tab[rr * DC + k];
                     const int jv = __ldg(o.chk_var + (size_t)rows[rr] * DC + k);
                     return jv >= 0 ? (int)pos[jv] : -1;
                 },
@@ -179,13 +187,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
                     return (sg[c >> 5] >> (c & 31)) & 1u;
                 });
             const bool bad = !ok;
-            const uint32_t xw = ok ? gf2::back_substitute(lockw, specw, up, (n + 31) >> 5, n) : 0u;
+            const uint32_t xw = ok ? gf2::back_substitute(lockw, specw, up, nw, n) : 0u;
             s_x[lane] = xw;
             if (lane == 0 && bad) s_bad = 1;
         }
         __syncthreads();
 
-        // 5. scatter x to the faults of R
+        // 6. scatter x to the faults of R
         if (s_bad) {
             if (tid == 0) {
                 out.status[shot] = -2;
