@@ -724,25 +724,33 @@ def soft_dmem_variant(args, dev, stream, flush, B=4096):
     F = sample_faults_t(P.p, 20, B, device=dev)
     syn = pack_bits_t(syndromes_t(P.H, F))
     faults = pack_bits_t(F)
-    soft = SoftDMem(P.row_ptr, P.col_idx, P.p, T, 5, torch.float32, device=dev.index)
     gamma = torch.full((P.N,), 0.125, dtype=torch.float32, device=dev)
     alpha = torch.ones(T, dtype=torch.float32, device=dev)
-    ws = soft.workspace(B)
-    fwd, bwd = [], []
-    for k in range(8):
-        flush.zero_()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        with torch.cuda.stream(stream):
-            e[0].record(stream)
-            loss, _, _ = soft.forward(syn, faults, gamma, alpha, ws, stream=stream)
-            e[1].record(stream)
-            gg, ga = soft.backward(syn, faults, gamma, alpha, ws, stream=stream)
-            e[2].record(stream)
-        torch.cuda.synchronize()
-        if k >= 3:
-            fwd.append(e[0].elapsed_time(e[1]))
-            bwd.append(e[1].elapsed_time(e[2]))
-    f_ms, b_ms = sum(fwd) / len(fwd), sum(bwd) / len(bwd)
+
+    def time_step(K):
+        soft = SoftDMem(P.row_ptr, P.col_idx, P.p, T, K, torch.float32, device=dev.index)
+        ws = soft.workspace(B)
+        fwd, bwd = [], []
+        for k in range(8):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            with torch.cuda.stream(stream):
+                e[0].record(stream)
+                loss, _, _ = soft.forward(syn, faults, gamma, alpha, ws, stream=stream)
+                e[1].record(stream)
+                gg, ga = soft.backward(syn, faults, gamma, alpha, ws, stream=stream)
+                e[2].record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                fwd.append(e[0].elapsed_time(e[1]))
+                bwd.append(e[1].elapsed_time(e[2]))
+        nbytes = ws.numel()
+        soft.close()
+        return sum(fwd) / len(fwd), sum(bwd) / len(bwd), loss, gg, nbytes
+
+    # every state stored (no recompute in the adjoint): 25 checkpoints per shot
+    f1_ms, b1_ms, _, _, ws1 = time_step(1)
+    f_ms, b_ms, loss, gg, ws5 = time_step(5)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     out = {"workload": f"gross T=12 p=0.003, batch {B}, 25 iterations, checkpoint every 5, "
                        "float32, gamma_j (2736) and alpha_t (25) trainable",
@@ -753,7 +761,16 @@ def soft_dmem_variant(args, dev, stream, flush, B=4096):
            "backward_roofline": soft_roofline(P.E * T * B, b_ms,
                                               soft_backward_ops_per_edge_iter(T, 5), sms),
            "loss": float(loss.item()),
-           "grad_gamma_norm": float(gg.norm().item())}
+           "grad_gamma_norm": float(gg.norm().item()),
+           "workspace_bytes": ws5,
+           # the same step with every state a checkpoint: the forward stores 25 states per
+           # shot, the adjoint recomputes nothing
+           "checkpoint_every_1": {"forward_ms": f1_ms, "backward_ms": b1_ms,
+                                  "step_shots_per_s": B / ((f1_ms + b1_ms) / 1e3),
+                                  "workspace_bytes": ws1,
+                                  "backward_roofline": soft_roofline(
+                                      P.E * T * B, b1_ms, soft_backward_ops_per_edge_iter(T, 1),
+                                      sms)}}
     if args.cpu_baseline:
         from oracle.soft import soft_dmem
         n = 64
@@ -765,7 +782,6 @@ def soft_dmem_variant(args, dev, stream, flush, B=4096):
         out["cpu_baseline"] = {"value": n / dt, "unit": "shots/s (forward + gradient)",
                                "cores": os.cpu_count(), "kind": "oracle",
                                "sample": f"{n} shots, FP64, full trajectory stored"}
-    soft.close()
     return out
 
 
