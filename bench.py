@@ -488,6 +488,11 @@ def post_processing_variants(args, dev, stream, flush, block_threads=0):
            "osd": f"25 plain BP iterations, Lambda_confident={conf}, |R|_max={rmax}",
            "first_leg_ms": ms_first, "first_leg_failures": todo,
            "osd_ms": ms_osd, "osd_shots_per_s": todo / (ms_osd / 1e3) if todo else None,
+           # the BP share of the launch: its 25 float32 iterations per post-processed shot
+           # against the shared-memory roof (the ranking, the sort and the elimination are
+           # not counted, so this is a lower bound on the launch's use of the SM)
+           "osd_bp_roofline": decode_roofline(P.E, P.N, 25 * todo, ms_osd, "fp32",
+                                              first.info.num_sms, sm_max_mhz()),
            "osd_status": {"solved": int((st == QLDPC_OSD_SOLVED).sum().item()),
                           "too_many": int((st == QLDPC_OSD_TOO_MANY).sum().item()),
                           "no_solution": int((st == QLDPC_OSD_NO_SOLUTION).sum().item())},
@@ -519,6 +524,10 @@ def post_processing_variants(args, dev, stream, flush, block_threads=0):
                                   f"interior faults <= 512",
                        "ms": ms_cl,
                        "shots_per_s": todo / (ms_cl / 1e3) if todo else None,
+                       # the BP share, as for filtered-OSD (growth steps and validity
+                       # tests not counted)
+                       "bp_roofline": decode_roofline(P.E, P.N, 25 * todo, ms_cl, "fp32",
+                                                      first.info.num_sms, sm_max_mhz()),
                        "decoded": int((stc == QLDPC_CLUSTER_DECODED).sum().item()),
                        "failed": int((stc < 0).sum().item()),
                        "mean_growth_steps": float(steps_cl[skip == 0].float().mean().item())
