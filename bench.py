@@ -249,10 +249,15 @@ def kernel_source_sha1() -> str:
     return h.hexdigest()[:12]
 
 
-def profile_field(name: str):
-    """A value recorded in the committed ncu summary of the decode kernel, or None when
-    the summary is absent or was taken on a different kernel source."""
-    path = os.path.join(ROOT, "profiles", "fused_decode_gross_T12.md")
+PROFILE_FP32 = "fused_decode_gross_T12.md"
+PROFILE_FP16 = "fused_decode_gross_T12_fp16.md"
+
+
+def profile_field(name: str, profile: str = PROFILE_FP32):
+    """A value recorded in a committed ncu summary of the decode kernel (float32 by
+    default), or None when the summary is absent or was taken on a different kernel
+    source."""
+    path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     same, val = False, None
@@ -264,7 +269,7 @@ def profile_field(name: str):
     return val if same else None
 
 
-def traffic_per_launch(args):
+def traffic_per_launch(args, profile: str = PROFILE_FP32):
     """DRAM bytes (read + write) of one decode launch, from the committed ncu summary.
 
     profiles/fused_decode_gross_T12.md records dram__bytes_read.sum and
@@ -274,7 +279,7 @@ def traffic_per_launch(args):
     was taken on a different kernel source (the sha1 of KERNEL_SOURCES is recorded in the
     summary).
     """
-    path = os.path.join(ROOT, "profiles", "fused_decode_gross_T12.md")
+    path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     sha = kernel_source_sha1()
@@ -878,7 +883,12 @@ def run_ours(args):
                           "identical_to_fp32_fused": same}
         if name == "fused_fp16":
             it16 = int(vo[3].to(torch.int64).sum().item())
-            variants[name]["roofline"] = decode_roofline(P.E, P.N, it16, vms, "fp16", sms, mhz)
+            r16 = decode_roofline(P.E, P.N, it16, vms, "fp16", sms, mhz,
+                                  traffic=traffic_per_launch(args, PROFILE_FP16))
+            r16["issue_slots_used_frac"] = (lambda v: v / 100.0 if v is not None else None)(
+                profile_field("smsp__issue_active.avg.pct_of_peak_sustained_active",
+                              PROFILE_FP16))
+            variants[name]["roofline"] = r16
             variants[name]["speedup_vs_fused_fp32"] = ms / vms
         vd.close()
     variants["fused_fp32_speedup_vs_baseline"] = (value / ws) / variants["baseline_fp32"]["value"]
