@@ -14,10 +14,9 @@
 //   4. update loop (Sec. 6.4-6.7): the first invalid cluster c is grown by every
 //      neighbour of its vertices, every cluster the grown set meets is merged into c
 //      (and leaves the invalid list), the interior faults of c are found, and c is
-//      tested by the GF(2) solver of one warp (gf2_warp.cuh) on its checks (rows,
-//      increasing index) and interior faults (columns, increasing index): dense
-//      elimination when the system fits the solver's region, else the streaming
-//      solver; an invalid c goes to the end of the list;
+//      tested by the streaming GF(2) solver of one warp (gf2_warp.cuh, several rows in
+//      flight) on its checks (rows, increasing index) and interior faults (columns,
+//      increasing index); an invalid c goes to the end of the list;
 //   5. output (Sec. 6.8): each surviving cluster's solution with free columns 0; the
 //      correction is F_pre + the union of those.
 //

@@ -156,7 +156,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
         const int nw = (n + 31) >> 5;
         const size_t piv_words = ((size_t)n * nw + 3) & ~(size_t)3;
         int16_t *tab = reinterpret_cast<int16_t *>(up + piv_words);
-        const int tab_rows = (int)((L.region_bytes - 4 * piv_words) / (2 * DC));
+        const size_t piv_bytes = 4 * piv_words;  // <= region_bytes, as n <= max_cand
+        const int tab_rows =
+            piv_bytes < L.region_bytes ? (int)((L.region_bytes - piv_bytes) / (2 * DC)) : 0;
         if (!s_bad)
             for (int c = tid; c < g.M; c += NT) {
                 if (!((par[c >> 5] >> (c & 31)) & 1u)) continue;
