@@ -1024,8 +1024,8 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
         const int d = row_ptr[i + 1] - row_ptr[i];
         rp[i] = pad ? 8 * i : row_ptr[i];
         deg[i] = d;
-        for (int k = 0; k < (pad ? 8 : d); ++k)
-            ci[rp[i] + k] = col_idx[row_ptr[i] + (k < d ? k : 0)];
+        for (int k = 0; k < (pad ? 8 : d); ++k)  // padding slots: the row's first fault (0 if none)
+            ci[rp[i] + k] = d > 0 ? col_idx[row_ptr[i] + (k < d ? k : 0)] : 0;
     }
     rp[M] = slots;
     std::vector<int32_t> var_ptr(N + 1, 0), var_edges(std::max(slots, 1)), fill(N, 0);

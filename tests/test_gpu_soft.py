@@ -210,3 +210,28 @@ def test_fp32_tracks_fp64_oracle_on_a_14_round_gross_graph():
     assert np.abs(gg.cpu().numpy() - gg_ref).max() <= 1e-3 * np.abs(gg_ref).max()
     assert np.abs(ga.cpu().numpy() - ga_ref).max() <= 1e-3 * np.abs(ga_ref).max()
     soft.close()
+
+
+def test_fp32_padded_rows_with_empty_and_short_checks():
+    """float32 pads check rows to 8 slots; rows of degree 0 and of degree below 8 (the
+    72-qubit code-capacity rows have 6) keep their padding slots out of every product:
+    the 72-qubit case with an empty check appended first and last, against the oracle."""
+    P, F, s, gam, alpha = _case(seed=8)
+    rp = np.concatenate([[0], P.row_ptr, [P.row_ptr[-1]]]).astype(np.int32)
+    s2 = np.concatenate([np.zeros((s.shape[0], 1), s.dtype), s,
+                         np.zeros((s.shape[0], 1), s.dtype)], axis=1)
+    g32 = gam.astype(np.float32).astype(np.float64)
+    a32 = alpha.astype(np.float32).astype(np.float64)
+    L_ref, gg_ref, ga_ref, m_ref = soft_dmem(rp, P.col_idx, P.p, g32, a32, s2, F, eps=EPS32,
+                                             marginals=True)
+    soft = SoftDMem(rp, P.col_idx, P.p, iterations=25, checkpoint_every=5)
+    syn, flt, g, a = _dev(P, F, s2, g32, a32, torch.float32)
+    loss, marg, ws = soft.forward(syn, flt, g, a, marginals=True)
+    gg, ga = soft.backward(syn, flt, g, a, ws)
+    torch.cuda.synchronize()
+    err = np.abs(marg.cpu().numpy() - m_ref) / np.maximum(1.0, np.abs(m_ref))
+    assert err.max() <= 1e-4, err.max()
+    assert abs(loss.item() - L_ref) <= 1e-4 * L_ref
+    assert np.abs(gg.cpu().numpy() - gg_ref).max() <= 1e-3 * np.abs(gg_ref).max()
+    assert np.abs(ga.cpu().numpy() - ga_ref).max() <= 1e-3 * np.abs(ga_ref).max()
+    soft.close()
