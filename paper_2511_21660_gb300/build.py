@@ -25,7 +25,8 @@ FUSED_FAMILIES = [(0, 8, 4), (0, 16, 8), (0, 32, 8), (1, 8, 4), (1, 16, 8), (1, 
 
 
 def _units():
-    units = [("qldpc_api", "qldpc_api.cu", []), ("relay_baseline", "relay_baseline.cu", []),
+    units = [("qldpc_api", "qldpc_api.cu", []), ("soft_api", "soft_api.cu", []),
+             ("post_api", "post_api.cu", []), ("relay_baseline", "relay_baseline.cu", []),
              ("soft_dmem", "soft_dmem.cu", []), ("filtered_osd", "filtered_osd.cu", []),
              ("cluster_decode", "cluster_decode.cu", [])]
     for f16, dc, dv in FUSED_FAMILIES:

@@ -24,6 +24,7 @@
 // instead of one bitmap per cluster: growth, merge detection and relabelling are then
 // three block-wide passes over the vertices, whatever the number of clusters.
 #include "gf2_warp.cuh"
+#include "post_internal.h"
 #include "relay_device.cuh"
 
 namespace qldpc {

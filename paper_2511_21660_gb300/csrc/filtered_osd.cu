@@ -21,6 +21,7 @@
 //
 // A row is a bitset over ranking positions, 32 columns per word.
 #include "gf2_warp.cuh"
+#include "post_internal.h"
 #include "relay_device.cuh"
 
 namespace qldpc {

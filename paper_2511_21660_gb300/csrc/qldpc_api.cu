@@ -1,5 +1,6 @@
-// Host side of the C ABI declared in include/qldpc.h: input validation, graph
-// layout for the kernels, kernel selection, launches and buffer staging.
+// Host side of the Relay decoder's C ABI (include/qldpc.h): input validation, graph
+// layout for the kernels, kernel selection, launches and buffer staging.  The soft
+// DMem-BP leg's entry points are in soft_api.cu, the post-processors' in post_api.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -10,14 +11,15 @@
 
 #include <cuda_fp16.h>
 
-#include "qldpc.h"
-#include "qldpc_internal.h"
+#include "api_common.h"
 
 using namespace qldpc;
 
-namespace {
+namespace qldpc {
 
-thread_local std::string g_last_error;
+static thread_local std::string g_last_error;
+
+std::string &last_error() { return g_last_error; }
 
 int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -28,65 +30,6 @@ int fail(int code, const char *fmt, ...) {
     g_last_error = buf;
     return code;
 }
-
-#define QL_CUDA(call)                                                                    \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess) {                                                         \
-            int code_ = e_ == cudaErrorMemoryAllocation ? QLDPC_ERR_OOM : QLDPC_ERR_CUDA; \
-            return fail(code_, "%s failed: %s", #call, cudaGetErrorString(e_));          \
-        }                                                                                \
-    } while (0)
-
-// Makes `dev` current for the scope and restores the caller's device afterwards.
-struct DeviceGuard {
-    int prev = -1;
-    cudaError_t err = cudaSuccess;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) err = cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-}  // namespace
-
-struct qldpc_decoder {
-    int device = 0;
-    int M = 0, N = 0, E = 0, dc_max = 0, dv_max = 0;
-    DevParams prm{};
-    int kernel = QLDPC_KERNEL_FUSED;
-    int msg_fp16 = 0;
-    const FusedKernel *fk = nullptr;        // decode kernel
-    const FusedKernel *fk_trace = nullptr;  // trace kernel
-    size_t trace_smem = 0;
-    int block_threads = 0, blocks_per_sm = 0, num_sms = 0, grid = 0;
-    size_t smem = 0;
-    FusedGraph fg{};
-    BaseGraph bg{};
-    void *arena = nullptr;
-    unsigned int *counter = nullptr;  // [0] work counter, [1] tail records, [2] records taken
-    // tail continuation (fused kernel): the resuming launch's kernel and grid, the records
-    const FusedKernel *fk_tail = nullptr;
-    int tail_grid = 0;
-    TailCont tail{};  // mode 0 when off
-    void *tail_arena = nullptr;
-    cudaStream_t stream = nullptr;  // internal stream of the host-buffer entry point
-    void *stage = nullptr;
-    int64_t stage_B = 0;
-    unsigned char *static_scratch = nullptr;  // device address of the static staging array
-};
-
-namespace {
-int lookup_static_scratch(qldpc_decoder *d);
-}
-
-namespace {
 
 int validate_graph(int32_t M, int32_t N, const int32_t *row_ptr, const int32_t *col_idx,
                    const double *priors) {
@@ -110,6 +53,32 @@ int validate_graph(int32_t M, int32_t N, const int32_t *row_ptr, const int32_t *
             return fail(QLDPC_ERR_INVALID_ARG, "prior %d = %g outside (0, 1)", j, priors[j]);
     return QLDPC_OK;
 }
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_batch(const qldpc_decoder *d, const void *syn, int64_t B, const void *corr) {
+    if (!d) return fail(QLDPC_ERR_INVALID_ARG, "decoder handle is NULL");
+    if (B < 0 || B > 0x7fffffffLL) return fail(QLDPC_ERR_INVALID_ARG, "batch size %lld out of range", (long long)B);
+    if (B > 0 && (!syn || !corr)) return fail(QLDPC_ERR_INVALID_ARG, "syndromes and corrections must not be NULL");
+    return QLDPC_OK;
+}
+
+}  // namespace qldpc
+
+
+namespace {
+int lookup_static_scratch(qldpc_decoder *d);
+}
+
+namespace {
+
 
 int validate_params(const qldpc_relay_params *p, int N) {
     if (!p) return fail(QLDPC_ERR_INVALID_ARG, "params must not be NULL");
@@ -136,14 +105,6 @@ int validate_params(const qldpc_relay_params *p, int N) {
     return QLDPC_OK;
 }
 
-bool is_device_ptr(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 // Picks the compiled fused-kernel family for the graph's degrees.
 int pick_family(int dc, int dv, int fp16, const FusedKernel **tab, int *n) {
@@ -460,12 +421,6 @@ int launch(qldpc_decoder *d, const uint64_t *syn, int64_t B, DecodeOut out, cuda
                              ShotMap{nullptr, nullptr, d->fg.syn_words, d->fg.cor_words}, st);
 }
 
-int check_batch(const qldpc_decoder *d, const void *syn, int64_t B, const void *corr) {
-    if (!d) return fail(QLDPC_ERR_INVALID_ARG, "decoder handle is NULL");
-    if (B < 0 || B > 0x7fffffffLL) return fail(QLDPC_ERR_INVALID_ARG, "batch size %lld out of range", (long long)B);
-    if (B > 0 && (!syn || !corr)) return fail(QLDPC_ERR_INVALID_ARG, "syndromes and corrections must not be NULL");
-    return QLDPC_OK;
-}
 
 }  // namespace
 
@@ -911,618 +866,3 @@ const char *qldpc_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
 
-// ---- soft DMem-BP (sum-product leg with trainable gamma_j, alpha_t) -------------------
-
-struct qldpc_soft {
-    int device = 0;
-    int M = 0, N = 0, E = 0, dc_max = 0, dv_max = 0;
-    int T = 0, K = 0, fp64 = 0;
-    double eps = 0;
-    SoftGraph g{};
-    void *arena = nullptr;
-    void *w = nullptr;  // prior LLRs in the working precision
-};
-
-namespace {
-
-size_t soft_workspace_layout(const qldpc_soft *s, int64_t B, size_t off[6]) {
-    const size_t rs = s->fp64 ? 8 : 4, EN = (size_t)s->g.E + s->N;  // edge slots + faults
-    const int nck = (s->T + s->K - 1) / s->K;
-    const size_t sz[6] = {(size_t)B * nck * EN * rs, (size_t)B * s->K * EN * rs, (size_t)B * rs,
-                          (size_t)B * s->N * rs, (size_t)B * s->T * rs, (size_t)B * s->N * rs};
-    size_t o = 0;
-    for (int q = 0; q < 6; ++q) {
-        off[q] = o;
-        o = align_up(o + sz[q], 256);
-    }
-    return o;
-}
-
-int soft_check_call(const qldpc_soft *s, const uint64_t *syn, const uint64_t *faults, int64_t B,
-                    const void *gamma, const void *alpha, void *ws, uint64_t ws_bytes,
-                    size_t off[6]) {
-    if (!s) return fail(QLDPC_ERR_INVALID_ARG, "soft handle is NULL");
-    if (B < 1 || B > 0x7fffffffLL) return fail(QLDPC_ERR_INVALID_ARG, "batch size out of range");
-    if (!syn || !faults || !gamma || !alpha || !ws)
-        return fail(QLDPC_ERR_INVALID_ARG, "syndromes, faults, gamma, alpha and workspace are required");
-    const size_t need = soft_workspace_layout(s, B, off);
-    if (ws_bytes < need)
-        return fail(QLDPC_ERR_INVALID_ARG, "workspace of %llu bytes, %zu needed",
-                    (unsigned long long)ws_bytes, need);
-    const void *ptrs[5] = {syn, faults, gamma, alpha, ws};
-    for (int q = 0; q < 5; ++q)
-        if (!is_device_ptr(ptrs[q]))
-            return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
-    return QLDPC_OK;
-}
-
-SoftLaunch soft_launch(const qldpc_soft *s, const uint64_t *syn, const uint64_t *faults,
-                       int64_t B, const void *gamma, const void *alpha, void *ws,
-                       const size_t off[6]) {
-    SoftLaunch L{};
-    char *base = static_cast<char *>(ws);
-    L.g = s->g;
-    L.fp64 = s->fp64;
-    L.dc_max = s->dc_max;
-    L.T_it = s->T;
-    L.K = s->K;
-    L.B = (int)B;
-    L.eps = s->eps;
-    L.syn = syn;
-    L.faults = faults;
-    L.gamma = gamma;
-    L.alpha = alpha;
-    L.w = s->w;
-    L.ckpt = base + off[0];
-    L.seg = base + off[1];
-    L.shot_loss = base + off[2];
-    L.shot_gg = base + off[3];
-    L.shot_ga = base + off[4];
-    L.shot_lb = base + off[5];
-    return L;
-}
-
-}  // namespace
-
-extern "C" {
-
-int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row_ptr,
-                      const int32_t *col_idx, const double *priors, int32_t iterations,
-                      int32_t checkpoint_every, int32_t real_type, int device) {
-    g_last_error.clear();
-    if (!out) return fail(QLDPC_ERR_INVALID_ARG, "out must not be NULL");
-    *out = nullptr;
-    int rc = validate_graph(M, N, row_ptr, col_idx, priors);
-    if (rc) return rc;
-    if (iterations < 1) return fail(QLDPC_ERR_INVALID_ARG, "iterations must be >= 1");
-    if (checkpoint_every < 1 || checkpoint_every > iterations)
-        return fail(QLDPC_ERR_INVALID_ARG, "checkpoint_every must be in [1, iterations]");
-    if (real_type != QLDPC_REAL_FP32 && real_type != QLDPC_REAL_FP64)
-        return fail(QLDPC_ERR_INVALID_ARG, "unknown real_type %d", real_type);
-    int ndev = 0;
-    QL_CUDA(cudaGetDeviceCount(&ndev));
-    if (device < 0 || device >= ndev) return fail(QLDPC_ERR_INVALID_ARG, "device %d of %d", device, ndev);
-    DeviceGuard guard(device);
-    QL_CUDA(guard.err);
-    qldpc_soft *s = new (std::nothrow) qldpc_soft();
-    if (!s) return fail(QLDPC_ERR_OOM, "host allocation failed");
-    s->device = device;
-    s->M = M;
-    s->N = N;
-    s->E = row_ptr[M];
-    s->T = iterations;
-    s->K = checkpoint_every;
-    s->fp64 = real_type == QLDPC_REAL_FP64;
-    s->eps = s->fp64 ? 1e-15 : 1.1920928955078125e-07;  // |product| <= 1 - eps
-    for (int i = 0; i < M; ++i) s->dc_max = std::max(s->dc_max, row_ptr[i + 1] - row_ptr[i]);
-    // float32 rows of at most 8 edges are padded to 8 slots (row i: slots 8 i .. 8 i + 7),
-    // which the kernels read and write as 16-byte halves
-    const bool pad = !s->fp64 && s->dc_max <= 8;
-    const int slots = pad ? 8 * M : s->E;
-    std::vector<int32_t> rp(M + 1), deg(std::max(M, 1)), ci(std::max(slots, 1));
-    for (int i = 0; i < M; ++i) {
-        const int d = row_ptr[i + 1] - row_ptr[i];
-        rp[i] = pad ? 8 * i : row_ptr[i];
-        deg[i] = d;
-        for (int k = 0; k < (pad ? 8 : d); ++k)  // padding slots: the row's first fault (0 if none)
-            ci[rp[i] + k] = d > 0 ? col_idx[row_ptr[i] + (k < d ? k : 0)] : 0;
-    }
-    rp[M] = slots;
-    std::vector<int32_t> var_ptr(N + 1, 0), var_edges(std::max(slots, 1)), fill(N, 0);
-    for (int e = 0; e < s->E; ++e) var_ptr[col_idx[e] + 1]++;
-    for (int j = 0; j < N; ++j) {
-        s->dv_max = std::max(s->dv_max, var_ptr[j + 1]);
-        var_ptr[j + 1] += var_ptr[j];
-    }
-    for (int i = 0; i < M; ++i)
-        for (int k = 0; k < deg[i]; ++k) {
-            const int j = col_idx[row_ptr[i] + k];
-            var_edges[var_ptr[j] + fill[j]++] = rp[i] + k;
-        }
-    auto cleanup = [&](int code) {
-        std::string msg = g_last_error;
-        qldpc_soft_destroy(s);
-        g_last_error = msg;
-        return code;
-    };
-    if (s->dc_max > 32 || s->dv_max > 8)
-        return cleanup(fail(QLDPC_ERR_UNSUPPORTED, "check degree %d / fault degree %d above 32 / 8",
-                            s->dc_max, s->dv_max));
-    SoftGraph &g = s->g;
-    g.M = M;
-    g.N = N;
-    g.E = slots;
-    g.syn_words = (M + 63) / 64;
-    g.cor_words = (N + 63) / 64;
-    int optin = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    if (e != cudaSuccess) return cleanup(fail(QLDPC_ERR_CUDA, "%s", cudaGetErrorString(e)));
-    if (soft_smem_backward(g, s->T, s->fp64) > (size_t)optin)
-        return cleanup(fail(QLDPC_ERR_UNSUPPORTED, "soft state needs %zu B of shared memory, above %d",
-                            soft_smem_backward(g, s->T, s->fp64), optin));
-    const size_t rs = s->fp64 ? 8 : 4;
-    const size_t sizes[6] = {sizeof(int32_t) * (M + 1), sizeof(int32_t) * std::max(slots, 1),
-                             sizeof(int32_t) * (N + 1), sizeof(int32_t) * std::max(slots, 1),
-                             rs * N, sizeof(int32_t) * std::max(M, 1)};
-    size_t off[6], o = 0;
-    for (int q = 0; q < 6; ++q) {
-        off[q] = o;
-        o = align_up(o + sizes[q], 256);
-    }
-    e = cudaMalloc(&s->arena, o);
-    if (e != cudaSuccess) return cleanup(fail(QLDPC_ERR_OOM, "cudaMalloc: %s", cudaGetErrorString(e)));
-    std::vector<double> w64(N);
-    std::vector<float> w32(N);
-    for (int j = 0; j < N; ++j) {
-        w64[j] = std::log((1.0 - priors[j]) / priors[j]);
-        w32[j] = (float)w64[j];
-    }
-    char *base = static_cast<char *>(s->arena);
-    const void *src[6] = {rp.data(), ci.data(), var_ptr.data(), var_edges.data(),
-                          s->fp64 ? (const void *)w64.data() : (const void *)w32.data(),
-                          deg.data()};
-    for (int q = 0; q < 6; ++q) {
-        e = cudaMemcpy(base + off[q], src[q], sizes[q], cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cleanup(fail(QLDPC_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e)));
-    }
-    g.row_ptr = reinterpret_cast<const int32_t *>(base + off[0]);
-    g.col_idx = reinterpret_cast<const int32_t *>(base + off[1]);
-    g.var_ptr = reinterpret_cast<const int32_t *>(base + off[2]);
-    g.var_edges = reinterpret_cast<const int32_t *>(base + off[3]);
-    g.row_deg = pad ? reinterpret_cast<const int32_t *>(base + off[5]) : nullptr;
-    s->w = base + off[4];
-    *out = s;
-    return QLDPC_OK;
-}
-
-int qldpc_soft_workspace_bytes(const qldpc_soft *s, int64_t B, uint64_t *bytes) {
-    if (!s || !bytes || B < 0) return fail(QLDPC_ERR_INVALID_ARG, "bad argument");
-    size_t off[6];
-    *bytes = soft_workspace_layout(s, B, off);
-    return QLDPC_OK;
-}
-
-int qldpc_soft_forward(qldpc_soft *s, const uint64_t *syndromes, const uint64_t *faults, int64_t B,
-                       const void *gamma, const void *alpha, void *loss, void *marginals,
-                       void *workspace, uint64_t workspace_bytes, void *stream) {
-    g_last_error.clear();
-    size_t off[6];
-    int rc = soft_check_call(s, syndromes, faults, B, gamma, alpha, workspace, workspace_bytes, off);
-    if (rc) return rc;
-    if (!loss || !is_device_ptr(loss)) return fail(QLDPC_ERR_INVALID_ARG, "loss must be device memory");
-    if (marginals && !is_device_ptr(marginals))
-        return fail(QLDPC_ERR_INVALID_ARG, "marginals must be device memory");
-    DeviceGuard guard(s->device);
-    QL_CUDA(guard.err);
-    SoftLaunch L = soft_launch(s, syndromes, faults, B, gamma, alpha, workspace, off);
-    L.loss = loss;
-    L.marg = marginals;
-    QL_CUDA(soft_run_forward(L, static_cast<cudaStream_t>(stream)));
-    return QLDPC_OK;
-}
-
-int qldpc_soft_backward(qldpc_soft *s, const uint64_t *syndromes, const uint64_t *faults,
-                        int64_t B, const void *gamma, const void *alpha, const void *loss_grad,
-                        void *grad_gamma, void *grad_alpha, void *workspace,
-                        uint64_t workspace_bytes, void *stream) {
-    g_last_error.clear();
-    size_t off[6];
-    int rc = soft_check_call(s, syndromes, faults, B, gamma, alpha, workspace, workspace_bytes, off);
-    if (rc) return rc;
-    if (!grad_gamma || !grad_alpha || !is_device_ptr(grad_gamma) || !is_device_ptr(grad_alpha))
-        return fail(QLDPC_ERR_INVALID_ARG, "grad_gamma and grad_alpha must be device memory");
-    if (loss_grad && !is_device_ptr(loss_grad))
-        return fail(QLDPC_ERR_INVALID_ARG, "loss_grad must be device memory");
-    DeviceGuard guard(s->device);
-    QL_CUDA(guard.err);
-    SoftLaunch L = soft_launch(s, syndromes, faults, B, gamma, alpha, workspace, off);
-    L.upstream = loss_grad;
-    L.grad_gamma = grad_gamma;
-    L.grad_alpha = grad_alpha;
-    QL_CUDA(soft_run_backward(L, static_cast<cudaStream_t>(stream)));
-    return QLDPC_OK;
-}
-
-void qldpc_soft_destroy(qldpc_soft *s) {
-    if (!s) return;
-    DeviceGuard guard(s->device);
-    if (s->arena) cudaFree(s->arena);
-    delete s;
-}
-
-}  // extern "C"
-
-// ---- filtered-OSD post-processor ----------------------------------------------------
-
-namespace {
-
-// The faults of each check in CSR order, -1 past the check's degree: [Mp][DC].
-std::vector<int32_t> check_faults(int M, int Mp, int DC, const int32_t *row_ptr,
-                                  const int32_t *col_idx) {
-    std::vector<int32_t> cv((size_t)Mp * DC, -1);
-    for (int i = 0; i < M; ++i)
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-            cv[(size_t)i * DC + (e - row_ptr[i])] = col_idx[e];
-    return cv;
-}
-
-// The graph of a post-processor: a fused-layout decoder whose single gamma row is all
-// zeros, so that its first leg is plain min-sum BP of `bp_iters` iterations.
-int create_plain_bp(qldpc_decoder **out, int32_t M, int32_t N, const int32_t *row_ptr,
-                    const int32_t *col_idx, const double *priors, int bp_iters, int device) {
-    std::vector<float> zeros((size_t)N, 0.0f);
-    qldpc_relay_params rp{};
-    rp.tail_cut_iters = -1;
-    rp.legs_after_first = 0;
-    rp.iters_first = bp_iters > 0 ? bp_iters : 1;
-    rp.iters_later = 1;
-    rp.max_total_iters = 0;
-    rp.stop_after_solutions = 1;
-    rp.warm_start_mode = 0;
-    rp.msg_precision = QLDPC_MSG_FP32;
-    rp.kernel = QLDPC_KERNEL_FUSED;
-    rp.block_threads = 0;
-    rp.llr_clip = 0.0f;
-    rp.gamma_table = zeros.data();
-    return qldpc_create(out, M, N, row_ptr, col_idx, priors, &rp, device);
-}
-
-// Shared memory attribute, occupancy and grid of a post-processing kernel.
-cudaError_t configure_kernel(const void *fn, int threads, size_t smem, int device, int num_sms,
-                             int *grid, bool *fits) {
-    int optin = 0, bps = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    *fits = e == cudaSuccess && smem <= (size_t)optin;
-    if (e != cudaSuccess || !*fits) return e;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem);
-    *fits = e == cudaSuccess && bps >= 1;
-    *grid = num_sms * std::max(bps, 1);
-    return e;
-}
-
-}  // namespace
-
-// The shots a post-processor is to take: the indices b with skip[b] == 0, in any order
-// (each shot's result depends on its own inputs only), appended to list by warp-wide
-// ballots; count ends as their number.  Skipped shots get their status (and the extra
-// per-shot output) 0 here, so the post-processor visits only the listed shots.
-__global__ void compact_active(const uint8_t *__restrict__ skip, int B, int32_t *list,
-                               unsigned int *count, int32_t *status, int32_t *extra) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool act = b < B && !skip[b];
-    if (b < B && !act) {
-        status[b] = 0;
-        if (extra) extra[b] = 0;
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, act);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (act) list[base + __popc(m & ((1u << lane) - 1u))] = b;
-}
-
-// Post-processor work list: with a skip mask, the listed shots (the list grows with B on
-// the host, which then waits for the device); without one, every shot.  counter[0] is
-// the work counter, counter[1] the list's length.
-struct WorkList {
-    int32_t *list = nullptr;
-    int64_t cap = 0;
-};
-
-static cudaError_t prepare_work(WorkList &w, const uint8_t *skip, int64_t B, int32_t *status,
-                                int32_t *extra, unsigned int *counter, cudaStream_t st,
-                                const int32_t **list) {
-    cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), st);
-    *list = nullptr;
-    if (e != cudaSuccess || !skip) return e;
-    if (B > w.cap) {
-        if (w.list) {
-            e = cudaStreamSynchronize(st);
-            if (e == cudaSuccess) e = cudaFree(w.list);
-            w.list = nullptr;
-            w.cap = 0;
-            if (e != cudaSuccess) return e;
-        }
-        e = cudaMalloc(&w.list, sizeof(int32_t) * (size_t)B);
-        if (e != cudaSuccess) return e;
-        w.cap = B;
-    }
-    compact_active<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(skip, (int)B, w.list, counter + 1,
-                                                               status, extra);
-    *list = w.list;
-    return cudaGetLastError();
-}
-
-struct qldpc_osd {
-    int device = 0;
-    qldpc_decoder *bp = nullptr;  // fused graph of H (float32 messages, gamma row of zeros)
-    const OsdKernel *k = nullptr;
-    OsdArgs args{};
-    void *arena = nullptr;        // chk_var and the work counters
-    unsigned int *counter = nullptr;
-    WorkList work;
-    size_t smem = 0;
-    int grid = 0;
-};
-
-extern "C" {
-
-int qldpc_osd_create(qldpc_osd **out, int32_t M, int32_t N, const int32_t *row_ptr,
-                     const int32_t *col_idx, const double *priors,
-                     const qldpc_osd_params *params, int device) {
-    g_last_error.clear();
-    if (!out) return fail(QLDPC_ERR_INVALID_ARG, "out must not be NULL");
-    *out = nullptr;
-    if (!params) return fail(QLDPC_ERR_INVALID_ARG, "params must not be NULL");
-    if (params->bp_iters < 0) return fail(QLDPC_ERR_INVALID_ARG, "bp_iters < 0");
-    if (!std::isfinite(params->llr_confident))
-        return fail(QLDPC_ERR_INVALID_ARG, "llr_confident is not finite");
-    if (params->max_candidates < 1 || params->max_candidates > kOsdMaxCandidates)
-        return fail(QLDPC_ERR_INVALID_ARG, "max_candidates %d outside 1..%d",
-                    params->max_candidates, kOsdMaxCandidates);
-    int rc = validate_graph(M, N, row_ptr, col_idx, priors);
-    if (rc) return rc;
-    if (N > 32767) return fail(QLDPC_ERR_UNSUPPORTED, "N = %d above 32767", N);
-    if (M > 32767) return fail(QLDPC_ERR_UNSUPPORTED, "M = %d above 32767", M);
-
-    qldpc_osd *o = new (std::nothrow) qldpc_osd();
-    if (!o) return fail(QLDPC_ERR_OOM, "host allocation failed");
-    o->device = device;
-    rc = create_plain_bp(&o->bp, M, N, row_ptr, col_idx, priors, params->bp_iters, device);
-    if (rc) {
-        delete o;
-        return rc;
-    }
-    DeviceGuard guard(device);
-    const qldpc_decoder *d = o->bp;
-    const int DC = d->fk->dc, DV = d->fk->dv;
-    const OsdKernel *tab = nullptr;
-    int ntab = 0;
-    osd_table(&tab, &ntab);
-    for (int q = 0; q < ntab && !o->k; ++q)
-        if (tab[q].dc == DC && tab[q].dv == DV && (long long)tab[q].threads * tab[q].vpt >= N)
-            o->k = &tab[q];
-    auto bail = [&](int code) {
-        std::string msg = g_last_error;
-        qldpc_osd_destroy(o);
-        g_last_error = msg;
-        return code;
-    };
-    if (!o->k) {
-        fail(QLDPC_ERR_UNSUPPORTED, "no compiled OSD kernel for N = %d", N);
-        return bail(QLDPC_ERR_UNSUPPORTED);
-    }
-    OsdArgs &a = o->args;
-    a.bp_iters = params->bp_iters;
-    a.llr_conf = params->llr_confident;
-    a.max_cand = params->max_candidates;
-    a.W = (a.max_cand + 31) / 32;
-    a.KP = 1;
-    while (a.KP < a.max_cand) a.KP <<= 1;
-
-    const std::vector<int32_t> chk_var = check_faults(M, d->fg.Mp, DC, row_ptr, col_idx);
-    const size_t cv_bytes = align_up(sizeof(int32_t) * chk_var.size(), 256);
-    cudaError_t e = cudaMalloc(&o->arena, cv_bytes + 256);
-    if (e != cudaSuccess) {
-        fail(QLDPC_ERR_OOM, "cudaMalloc failed: %s", cudaGetErrorString(e));
-        return bail(QLDPC_ERR_OOM);
-    }
-    e = cudaMemcpy(o->arena, chk_var.data(), sizeof(int32_t) * chk_var.size(),
-                   cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        a.chk_var = static_cast<const int32_t *>(o->arena);
-        o->counter = reinterpret_cast<unsigned int *>(static_cast<char *>(o->arena) + cv_bytes);
-        o->smem = osd_smem_bytes(d->fg, a);
-        bool fits = false;
-        e = configure_kernel(o->k->fn, o->k->threads, o->smem, device, d->num_sms, &o->grid,
-                             &fits);
-        if (e == cudaSuccess && !fits) {
-            fail(QLDPC_ERR_UNSUPPORTED, "the OSD stage (%zu B of shared memory) cannot be resident",
-                 o->smem);
-            return bail(QLDPC_ERR_UNSUPPORTED);
-        }
-    }
-    if (e != cudaSuccess) {
-        fail(QLDPC_ERR_CUDA, "OSD set-up failed: %s", cudaGetErrorString(e));
-        return bail(QLDPC_ERR_CUDA);
-    }
-    *out = o;
-    return QLDPC_OK;
-}
-
-int qldpc_osd_decode_batch(qldpc_osd *o, const uint64_t *syndromes, int64_t B,
-                           const uint8_t *skip, uint64_t *corrections, int32_t *status,
-                           int32_t *n_candidates, void *stream) {
-    g_last_error.clear();
-    if (!o) return fail(QLDPC_ERR_INVALID_ARG, "OSD handle is NULL");
-    int rc = check_batch(o->bp, syndromes, B, corrections);
-    if (rc) return rc;
-    if (B > 0 && !status) return fail(QLDPC_ERR_INVALID_ARG, "status must not be NULL");
-    if (B == 0) return QLDPC_OK;
-    DeviceGuard guard(o->device);
-    QL_CUDA(guard.err);
-    const void *ptrs[5] = {syndromes, skip, corrections, status, n_candidates};
-    for (int q = 0; q < 5; ++q)
-        if (ptrs[q] && !is_device_ptr(ptrs[q]))
-            return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int32_t *list = nullptr;
-    QL_CUDA(prepare_work(o->work, skip, B, status, n_candidates, o->counter, st, &list));
-    const int grid = (int)std::min<int64_t>(o->grid, B);
-    QL_CUDA(o->k->launch(dim3(grid), o->smem, st, o->bp->fg, o->bp->prm, o->args, syndromes,
-                         list, (int)B, OsdOut{corrections, status, n_candidates}, o->counter));
-    return QLDPC_OK;
-}
-
-void qldpc_osd_destroy(qldpc_osd *o) {
-    if (!o) return;
-    {
-        DeviceGuard guard(o->device);
-        if (o->arena) cudaFree(o->arena);  // waits for work that may still use it
-        if (o->work.list) cudaFree(o->work.list);
-    }
-    qldpc_destroy(o->bp);
-    delete o;
-}
-
-}  // extern "C"
-
-// ---- cluster decoder ------------------------------------------------------------------
-
-struct qldpc_cluster {
-    int device = 0;
-    qldpc_decoder *bp = nullptr;  // fused graph of H (float32 messages, gamma row of zeros)
-    const ClusterKernel *k = nullptr;
-    ClusterArgs args{};
-    void *arena = nullptr;        // chk_var and the work counters
-    unsigned int *counter = nullptr;
-    WorkList work;
-    size_t smem = 0;
-    int grid = 0;
-};
-
-extern "C" {
-
-int qldpc_cluster_create(qldpc_cluster **out, int32_t M, int32_t N, const int32_t *row_ptr,
-                         const int32_t *col_idx, const double *priors,
-                         const qldpc_cluster_params *params, int device) {
-    g_last_error.clear();
-    if (!out) return fail(QLDPC_ERR_INVALID_ARG, "out must not be NULL");
-    *out = nullptr;
-    if (!params) return fail(QLDPC_ERR_INVALID_ARG, "params must not be NULL");
-    if (params->bp_iters < 0) return fail(QLDPC_ERR_INVALID_ARG, "bp_iters < 0");
-    if (!std::isfinite(params->llr_accept) || !std::isfinite(params->llr_erase) ||
-        params->llr_erase < params->llr_accept)
-        return fail(QLDPC_ERR_INVALID_ARG, "need finite llr_accept <= llr_erase");
-    if (params->max_clusters < 1 || params->max_clusters > kClusterMaxClusters)
-        return fail(QLDPC_ERR_INVALID_ARG, "max_clusters %d outside 1..%d", params->max_clusters,
-                    kClusterMaxClusters);
-    if (params->max_cluster_faults < 1 || params->max_cluster_faults > kClusterMaxColumns)
-        return fail(QLDPC_ERR_INVALID_ARG, "max_cluster_faults %d outside 1..%d",
-                    params->max_cluster_faults, kClusterMaxColumns);
-    int rc = validate_graph(M, N, row_ptr, col_idx, priors);
-    if (rc) return rc;
-    if (M + N > 32767) return fail(QLDPC_ERR_UNSUPPORTED, "M + N = %d above 32767", M + N);
-    qldpc_cluster *o = new (std::nothrow) qldpc_cluster();
-    if (!o) return fail(QLDPC_ERR_OOM, "host allocation failed");
-    o->device = device;
-    rc = create_plain_bp(&o->bp, M, N, row_ptr, col_idx, priors, params->bp_iters, device);
-    if (rc) {
-        delete o;
-        return rc;
-    }
-    DeviceGuard guard(device);
-    const qldpc_decoder *d = o->bp;
-    const int DC = d->fk->dc, DV = d->fk->dv;
-    auto bail = [&](int code) {
-        std::string msg = g_last_error;
-        qldpc_cluster_destroy(o);
-        g_last_error = msg;
-        return code;
-    };
-    const ClusterKernel *tab = nullptr;
-    int ntab = 0;
-    cluster_table(&tab, &ntab);
-    for (int q = 0; q < ntab && !o->k; ++q)
-        if (tab[q].dc == DC && tab[q].dv == DV && (long long)tab[q].threads * tab[q].vpt >= N)
-            o->k = &tab[q];
-    if (!o->k) {
-        fail(QLDPC_ERR_UNSUPPORTED, "no compiled cluster kernel for N = %d", N);
-        return bail(QLDPC_ERR_UNSUPPORTED);
-    }
-    ClusterArgs &a = o->args;
-    a.bp_iters = params->bp_iters;
-    a.llr_accept = params->llr_accept;
-    a.llr_erase = params->llr_erase;
-    a.max_clusters = params->max_clusters;
-    a.max_cols = params->max_cluster_faults;
-    a.W = (a.max_cols + 31) / 32;
-    const std::vector<int32_t> chk_var = check_faults(M, d->fg.Mp, DC, row_ptr, col_idx);
-    const size_t cv_bytes = align_up(sizeof(int32_t) * chk_var.size(), 256);
-    cudaError_t e = cudaMalloc(&o->arena, cv_bytes + 256);
-    if (e != cudaSuccess) {
-        fail(QLDPC_ERR_OOM, "cudaMalloc failed: %s", cudaGetErrorString(e));
-        return bail(QLDPC_ERR_OOM);
-    }
-    e = cudaMemcpy(o->arena, chk_var.data(), sizeof(int32_t) * chk_var.size(),
-                   cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        a.chk_var = static_cast<const int32_t *>(o->arena);
-        o->counter = reinterpret_cast<unsigned int *>(static_cast<char *>(o->arena) + cv_bytes);
-        o->smem = cluster_smem_bytes(d->fg, a);
-        bool fits = false;
-        e = configure_kernel(o->k->fn, o->k->threads, o->smem, device, d->num_sms, &o->grid,
-                             &fits);
-        if (e == cudaSuccess && !fits) {
-            fail(QLDPC_ERR_UNSUPPORTED,
-                 "the cluster stage (%zu B of shared memory) cannot be resident", o->smem);
-            return bail(QLDPC_ERR_UNSUPPORTED);
-        }
-    }
-    if (e != cudaSuccess) {
-        fail(QLDPC_ERR_CUDA, "cluster set-up failed: %s", cudaGetErrorString(e));
-        return bail(QLDPC_ERR_CUDA);
-    }
-    *out = o;
-    return QLDPC_OK;
-}
-
-int qldpc_cluster_decode_batch(qldpc_cluster *o, const uint64_t *syndromes, int64_t B,
-                               const uint8_t *skip, uint64_t *corrections, int32_t *status,
-                               int32_t *steps, void *stream) {
-    g_last_error.clear();
-    if (!o) return fail(QLDPC_ERR_INVALID_ARG, "cluster handle is NULL");
-    int rc = check_batch(o->bp, syndromes, B, corrections);
-    if (rc) return rc;
-    if (B > 0 && !status) return fail(QLDPC_ERR_INVALID_ARG, "status must not be NULL");
-    if (B == 0) return QLDPC_OK;
-    DeviceGuard guard(o->device);
-    QL_CUDA(guard.err);
-    const void *ptrs[5] = {syndromes, skip, corrections, status, steps};
-    for (int q = 0; q < 5; ++q)
-        if (ptrs[q] && !is_device_ptr(ptrs[q]))
-            return fail(QLDPC_ERR_INVALID_ARG, "argument %d is not device memory", q);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int32_t *list = nullptr;
-    QL_CUDA(prepare_work(o->work, skip, B, status, steps, o->counter, st, &list));
-    const int grid = (int)std::min<int64_t>(o->grid, B);
-    QL_CUDA(o->k->launch(dim3(grid), o->smem, st, o->bp->fg, o->bp->prm, o->args, syndromes,
-                         list, (int)B, ClusterOut{corrections, status, steps}, o->counter));
-    return QLDPC_OK;
-}
-
-void qldpc_cluster_destroy(qldpc_cluster *o) {
-    if (!o) return;
-    {
-        DeviceGuard guard(o->device);
-        if (o->arena) cudaFree(o->arena);  // waits for work that may still use it
-        if (o->work.list) cudaFree(o->work.list);
-    }
-    qldpc_destroy(o->bp);
-    delete o;
-}
-
-}  // extern "C"

@@ -18,7 +18,7 @@
 // final iteration again (for Lambda(T)); in the others the recompute stops one
 // iteration short, and the state it ends on is the first reverse step's input.  Per-shot gradients are summed
 // over shots in a fixed order, so results are deterministic.
-#include "qldpc_internal.h"
+#include "soft_internal.h"
 
 namespace qldpc {
 namespace {
