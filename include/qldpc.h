@@ -244,7 +244,8 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
                       int32_t checkpoint_every, int32_t real_type, int device);
 
 /* Bytes of device workspace a batch of B shots needs (checkpoints, segment buffer,
- * per-shot partial results, the adjoint's per-shot scratch).  The caller allocates it. */
+ * per-shot partial results, the adjoint's per-shot scratch).  The caller allocates it,
+ * 16-byte aligned (forward and backward refuse another alignment with INVALID_ARG). */
 int qldpc_soft_workspace_bytes(const qldpc_soft *s, int64_t B, uint64_t *bytes);
 
 /* Forward.  Device pointers: syndromes [B][ceil(M/64)] uint64, faults [B][ceil(N/64)]

@@ -24,11 +24,14 @@ struct qldpc_soft {
 
 namespace {
 
+// Workspace arrays: checkpoints [B][nck][S], segment buffer [B][K][S] (S values per
+// state), per-shot loss [B], gamma gradient [B][N], alpha gradient [B][T], and the
+// adjoint state (of nu, then of Lambda) between segments [B][S].
 size_t soft_workspace_layout(const qldpc_soft *s, int64_t B, size_t off[6]) {
-    const size_t rs = s->fp64 ? 8 : 4, EN = (size_t)s->g.E + s->N;  // edge slots + faults
+    const size_t rs = s->fp64 ? 8 : 4, S = (size_t)soft_state_values(s->g);
     const int nck = (s->T + s->K - 1) / s->K;
-    const size_t sz[6] = {(size_t)B * nck * EN * rs, (size_t)B * s->K * EN * rs, (size_t)B * rs,
-                          (size_t)B * s->N * rs, (size_t)B * s->T * rs, (size_t)B * s->N * rs};
+    const size_t sz[6] = {(size_t)B * nck * S * rs, (size_t)B * s->K * S * rs, (size_t)B * rs,
+                          (size_t)B * s->N * rs,     (size_t)B * s->T * rs,     (size_t)B * S * rs};
     size_t o = 0;
     for (int q = 0; q < 6; ++q) {
         off[q] = o;
@@ -44,6 +47,8 @@ int soft_check_call(const qldpc_soft *s, const uint64_t *syn, const uint64_t *fa
     if (B < 1 || B > 0x7fffffffLL) return fail(QLDPC_ERR_INVALID_ARG, "batch size out of range");
     if (!syn || !faults || !gamma || !alpha || !ws)
         return fail(QLDPC_ERR_INVALID_ARG, "syndromes, faults, gamma, alpha and workspace are required");
+    if (reinterpret_cast<uintptr_t>(ws) % 16 != 0)
+        return fail(QLDPC_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
     const size_t need = soft_workspace_layout(s, B, off);
     if (ws_bytes < need)
         return fail(QLDPC_ERR_INVALID_ARG, "workspace of %llu bytes, %zu needed",
@@ -77,7 +82,7 @@ SoftLaunch soft_launch(const qldpc_soft *s, const uint64_t *syn, const uint64_t 
     L.shot_loss = base + off[2];
     L.shot_gg = base + off[3];
     L.shot_ga = base + off[4];
-    L.shot_lb = base + off[5];
+    L.shot_adj = base + off[5];
     return L;
 }
 
@@ -159,12 +164,25 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
     if (soft_smem_backward(g, s->T, s->fp64) > (size_t)optin)
         return cleanup(fail(QLDPC_ERR_UNSUPPORTED, "soft state needs %zu B of shared memory, above %d",
                             soft_smem_backward(g, s->T, s->fp64), optin));
+    // one 8-byte record per fault (its first three slots and its degree) replaces the two
+    // dependent reads of var_ptr and var_edges in the kernels' fault loops
+    const bool rec = pad && slots < 65536;
+    std::vector<uint32_t> frec(2 * (size_t)std::max(N, 1), 0u);
+    if (rec)
+        for (int j = 0; j < N; ++j) {
+            const int b = var_ptr[j], d = var_ptr[j + 1] - b;
+            uint32_t sl[3];
+            for (int k = 0; k < 3; ++k) sl[k] = (uint32_t)(d > 0 ? var_edges[b + (k < d ? k : 0)] : 0);
+            frec[2 * j] = sl[0] | (sl[1] << 16);
+            frec[2 * j + 1] = sl[2] | ((uint32_t)d << 16);
+        }
     const size_t rs = s->fp64 ? 8 : 4;
-    const size_t sizes[6] = {sizeof(int32_t) * (M + 1), sizeof(int32_t) * std::max(slots, 1),
+    const size_t sizes[7] = {sizeof(int32_t) * (M + 1), sizeof(int32_t) * std::max(slots, 1),
                              sizeof(int32_t) * (N + 1), sizeof(int32_t) * std::max(slots, 1),
-                             rs * N, sizeof(int32_t) * std::max(M, 1)};
-    size_t off[6], o = 0;
-    for (int q = 0; q < 6; ++q) {
+                             rs * N, sizeof(int32_t) * std::max(M, 1),
+                             sizeof(uint32_t) * frec.size()};
+    size_t off[7], o = 0;
+    for (int q = 0; q < 7; ++q) {
         off[q] = o;
         o = align_up(o + sizes[q], 256);
     }
@@ -177,10 +195,10 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
         w32[j] = (float)w64[j];
     }
     char *base = static_cast<char *>(s->arena);
-    const void *src[6] = {rp.data(), ci.data(), var_ptr.data(), var_edges.data(),
+    const void *src[7] = {rp.data(), ci.data(), var_ptr.data(), var_edges.data(),
                           s->fp64 ? (const void *)w64.data() : (const void *)w32.data(),
-                          deg.data()};
-    for (int q = 0; q < 6; ++q) {
+                          deg.data(), frec.data()};
+    for (int q = 0; q < 7; ++q) {
         e = cudaMemcpy(base + off[q], src[q], sizes[q], cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cleanup(fail(QLDPC_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e)));
     }
@@ -189,6 +207,7 @@ int qldpc_soft_create(qldpc_soft **out, int32_t M, int32_t N, const int32_t *row
     g.var_ptr = reinterpret_cast<const int32_t *>(base + off[2]);
     g.var_edges = reinterpret_cast<const int32_t *>(base + off[3]);
     g.row_deg = pad ? reinterpret_cast<const int32_t *>(base + off[5]) : nullptr;
+    g.fault_rec = rec ? reinterpret_cast<const uint2 *>(base + off[6]) : nullptr;
     s->w = base + off[4];
     *out = s;
     return QLDPC_OK;

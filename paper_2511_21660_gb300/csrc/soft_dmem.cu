@@ -24,6 +24,9 @@ namespace qldpc {
 namespace {
 
 constexpr int SOFT_THREADS = 256;
+#ifndef SOFT_BWD_MINB
+#define SOFT_BWD_MINB 5
+#endif
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
@@ -70,13 +73,14 @@ struct SoftArgs {
     const uint64_t *syn, *faults;
     int B;
     const T *gamma, *alpha, *w;
-    T *ckpt;       // [B][nck][E+N]
-    T *seg;        // [B][K][E+N]
+    T *ckpt;       // [B][nck][sst] states (nu then Lambda, stride sst)
+    T *seg;        // [B][K][sst]
     T *shot_loss;  // [B]
     T *shot_gg;    // [B][N]
     T *shot_ga;    // [B][T]
-    T *shot_lb;    // [B][N] adjoint of Lambda (backward scratch)
+    T *shot_adj;   // [B][sst] nb and Lb between segments (backward scratch)
     T *marg;       // [B][N] or nullptr
+    int sst;       // values per stored state: E + N rounded up to a multiple of 4
 };
 
 __device__ __forceinline__ uint32_t bit_of(const uint64_t *v, int i) {
@@ -136,8 +140,38 @@ __device__ __forceinline__ void store_row(T *row, int i, int d, const T (&v)[DCM
 }
 
 __device__ __forceinline__ void row_span(const SoftGraph &g, int i, int &e0, int &d) {
-    e0 = g.row_ptr[i];
-    d = g.row_deg ? g.row_deg[i] : g.row_ptr[i + 1] - e0;
+    if (g.row_deg) {  // padded rows: row i is slots 8 i .. 8 i + 7
+        e0 = 8 * i;
+        d = g.row_deg[i];
+    } else {
+        e0 = g.row_ptr[i];
+        d = g.row_ptr[i + 1] - e0;
+    }
+}
+
+// Degree d of fault j and, for degrees 2 and 3, its slots e0, e1, e2 (increasing slot
+// order; e2 only for degree 3); b = its first var_edges entry, set for the other degrees
+// only (the generic loops).  One 8-byte record when the graph has them, else var_ptr
+// and var_edges.
+__device__ __forceinline__ void fault_slots(const SoftGraph &g, int j, int &d, int &b, int &e0,
+                                            int &e1, int &e2) {
+    if (g.fault_rec) {
+        const uint2 r = __ldg(g.fault_rec + j);
+        e0 = (int)(r.x & 0xffffu);
+        e1 = (int)(r.x >> 16);
+        e2 = (int)(r.y & 0xffffu);
+        d = (int)(r.y >> 16);
+        b = (d == 3 || d == 2) ? 0 : g.var_ptr[j];
+    } else {
+        b = g.var_ptr[j];
+        d = g.var_ptr[j + 1] - b;
+        e0 = e1 = e2 = 0;
+        if (d == 3 || d == 2) {
+            e0 = g.var_edges[b];
+            e1 = g.var_edges[b + 1];
+            if (d == 3) e2 = g.var_edges[b + 2];
+        }
+    }
 }
 
 // Check products of one row: P_k = prod_{l != k} tanh(nu_l/2), clamped.  The row
@@ -199,14 +233,13 @@ __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint6
     }
     __syncthreads();
     for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
-        const int b = g.var_ptr[j], d = g.var_ptr[j + 1] - b;
+        int d, b, e0, e1, e2;
+        fault_slots(g, j, d, b, e0, e1, e2);
         const T lam = (T(1) - a.gamma[j]) * a.w[j] + a.gamma[j] * Lam[j];
         // degrees 3 and 2 in registers, with the generic loop's order of additions
         if (d == 3 || d == 2) {
-            const int e0 = g.var_edges[b], e1 = g.var_edges[b + 1];
             const T m0 = nu[e0], m1 = nu[e1];
             if (d == 3) {
-                const int e2 = g.var_edges[b + 2];
                 const T m2 = nu[e2];
                 Lam[j] = lam + m0 + m1 + m2;
                 nu[e0] = lam + m1 + m2;
@@ -242,12 +275,30 @@ __device__ __forceinline__ void init_state(const SoftArgs<T> &a, T *nu, T *Lam) 
     __syncthreads();
 }
 
-template <typename T>
-__device__ __forceinline__ void copy_state(const T *src_nu, const T *src_L, T *dst, int E, int N) {
-    for (int e = threadIdx.x; e < E; e += SOFT_THREADS) dst[e] = src_nu[e];
-    for (int j = threadIdx.x; j < N; j += SOFT_THREADS) dst[E + j] = src_L[j];
+// Bulk prefetch of bytes (a multiple of 16) at a 16-byte aligned global address into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((unsigned)bytes)
+                 : "memory");
 }
 
+// Copy of n values (a state: nu then Lambda, contiguous in both places, or nu or its
+// adjoint alone).  float32 moves 16-byte vectors: every state starts on a 16-byte
+// boundary (the stride a.sst is a multiple of 4 values, the workspace is 16-byte
+// aligned) and n is a multiple of 4.
+template <typename T>
+__device__ __forceinline__ void copy_state(const T *src, T *dst, int n) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll 4
+        for (int q = threadIdx.x; q < n / 4; q += SOFT_THREADS) d4[q] = s4[q];
+    } else {
+        for (int e = threadIdx.x; e < n; e += SOFT_THREADS) dst[e] = src[e];
+    }
+}
+
+// Forward.  Shared memory: nu[E], Lam[N] (a.sst values).  The state before iterations
+// 1, K + 1, 2K + 1, ... is stored as a checkpoint.
 template <typename T, int DCM>
 __global__ void __launch_bounds__(SOFT_THREADS) soft_forward(SoftArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -258,11 +309,13 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_forward(SoftArgs<T> a) {
     const int b = blockIdx.x;
     const uint64_t *sy = a.syn + (size_t)b * g.syn_words;
     const uint64_t *fy = a.faults + (size_t)b * g.cor_words;
-    const size_t EN = (size_t)g.E + g.N;
+    const size_t S = (size_t)a.sst;
     init_state(a, nu, Lam);
     for (int t = 1; t <= a.T_it; ++t) {
-        if ((t - 1) % a.K == 0)
-            copy_state(nu, Lam, a.ckpt + ((size_t)b * a.nck + (t - 1) / a.K) * EN, g.E, g.N);
+        if ((t - 1) % a.K == 0) {
+            copy_state(nu, a.ckpt + ((size_t)b * a.nck + (t - 1) / a.K) * S, (int)S);
+            __syncthreads();  // copied before the check pass overwrites nu
+        }
         soft_iteration<T, DCM>(a, sy, t, nu, Lam);
     }
     T part = 0;
@@ -274,67 +327,75 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_forward(SoftArgs<T> a) {
     if (threadIdx.x == 0) a.shot_loss[b] = tot;
 }
 
-// Adjoint.  Shared memory: nu[E], Lam[N] (forward recompute, then each reverse step's
-// saved state), nb[E] (adjoint of nu(t), then of mu(t)), as[T] (alpha gradient of the
-// shot).  The adjoint of Lambda and the gamma gradient of fault j are touched only by
-// the thread that owns j, so they stay in global memory (shot_lb, shot_gg: coalesced,
-// cached), which keeps the block's shared state small enough for 3 blocks per SM.
+// Adjoint.  Shared memory holds a.sst + T values, as much as the forward's state, so
+// the adjoint runs as many blocks per SM as the forward:
+//   * the recompute of a segment runs the forward iterations on nu[E], Lam[N] and
+//     stores the state before each of the segment's iterations in the segment buffer;
+//   * the reverse steps keep nb[E] (adjoint of nu(t), then of mu(t)) in nu's place and
+//     Lb[N] (adjoint of Lambda) in Lam's place, and read the saved states from the
+//     segment buffer (the next step's state is prefetched into L2 by one bulk prefetch);
+//     during a recompute nb and Lb wait in global scratch (shot_adj);
+//   * as[T] (alpha gradient of the shot) follows the state.
+// The gamma gradient of fault j is touched only by the thread that owns j, so it stays
+// in global memory (shot_gg: coalesced, cached).
 template <typename T, int DCM>
-__global__ void __launch_bounds__(SOFT_THREADS) soft_backward(SoftArgs<T> a) {
+__global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD_MINB : 1)
+    soft_backward(SoftArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SoftGraph &g = a.g;
     T *nu = reinterpret_cast<T *>(smem_raw);
     T *Lam = nu + g.E;
-    T *nb = Lam + g.N;
-    T *as = nb + g.E;
+    T *nb = nu;
+    T *Lb = Lam;
+    T *as = nu + a.sst;
     __shared__ T red[SOFT_THREADS / 32];
     const int b = blockIdx.x;
-    T *Lb = a.shot_lb + (size_t)b * g.N;
     T *gs = a.shot_gg + (size_t)b * g.N;
     const uint64_t *sy = a.syn + (size_t)b * g.syn_words;
     const uint64_t *fy = a.faults + (size_t)b * g.cor_words;
-    const size_t EN = (size_t)g.E + g.N;
-    T *segb = a.seg + (size_t)b * a.K * EN;
+    const size_t S = (size_t)a.sst;
+    T *segb = a.seg + (size_t)b * a.K * S;
+    T *adj = a.shot_adj + (size_t)b * S;
     for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) gs[j] = 0;
     for (int t = threadIdx.x; t < a.T_it; t += SOFT_THREADS) as[t] = 0;
 
     for (int s = a.nck - 1; s >= 0; --s) {
         const int t0 = s * a.K, t1 = min(a.T_it, t0 + a.K);
         const bool last = s == a.nck - 1;
-        const T *ck = a.ckpt + ((size_t)b * a.nck + s) * EN;
-        for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nu[e] = ck[e];
-        for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) Lam[j] = ck[g.E + j];
-        __syncthreads();
-        // states before iterations t0+1 .. t1; iteration t1 itself runs only in the last
-        // segment, whose Lambda(T) seeds the adjoint; elsewhere the state before t1 stays
-        // in shared memory for the first reverse step
-        for (int t = t0 + 1; t <= (last ? t1 : t1 - 1); ++t) {
-            copy_state(nu, Lam, segb + (size_t)(t - t0 - 1) * EN, g.E, g.N);
-            soft_iteration<T, DCM>(a, sy, t, nu, Lam);
+        T *ck = a.ckpt + ((size_t)b * a.nck + s) * S;
+        if (!last) {  // nb and Lb of the segment after this one wait in global scratch
+            copy_state(nu, adj, (int)S);
+            __syncthreads();
         }
-        if (last) {  // Lambda(T) is in Lam: adjoint of the loss sum
+        copy_state(ck, nu, (int)S);  // nu, then Lam = nu + E
+        __syncthreads();
+        // the states before iterations t0+1 .. t1 go to the segment buffer; iteration t1
+        // itself runs only in the last segment, whose Lambda(T) seeds the adjoint
+        for (int t = t0 + 1; t <= t1; ++t) {
+            copy_state(nu, segb + (size_t)(t - t0 - 1) * S, (int)S);
+            __syncthreads();  // copied before the check pass overwrites nu
+            if (t < t1 || last) soft_iteration<T, DCM>(a, sy, t, nu, Lam);
+        }
+        if (last) {  // Lambda(T) is in Lam: Lb = adjoint of the loss sum, in place; nb = 0
             for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS)
                 Lb[j] = RM<T>::sigmoid(Lam[j]) - (bit_of(fy, j) ? T(0) : T(1));
             for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nb[e] = 0;
+        } else {
+            copy_state(adj, nu, (int)S);
         }
         __syncthreads();
         for (int t = t1; t > t0; --t) {
-            // the state before iteration t, staged in the forward arrays (free here; it is
-            // already there for the first reverse step of a segment that is not the last)
-            if (t < t1 || last)
-                copy_state(segb + (size_t)(t - t0 - 1) * EN,
-                           segb + (size_t)(t - t0 - 1) * EN + g.E, nu, g.E, g.N);
-            __syncthreads();
-            const T *nu_prev = nu;
-            const T *L_prev = Lam;
+            // the state before iteration t, from the segment buffer
+            const T *nu_prev = segb + (size_t)(t - t0 - 1) * S;
+            const T *L_prev = nu_prev + g.E;
+            if (threadIdx.x == 0 && t > t0 + 1) prefetch_l2(nu_prev - S, S * sizeof(T));
             const bool inner = t - 1 >= 1;
             // fault adjoint: lambda_bar = Lb + sum nb;  mu_bar_e = lambda_bar - nb_e
             for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
-                const int e0 = g.var_ptr[j], d = g.var_ptr[j + 1] - e0;
+                int d, e0, f0, f1, f2;
+                fault_slots(g, j, d, e0, f0, f1, f2);
                 T lb;
                 if (d == 3 || d == 2) {  // in registers, same order of additions
-                    const int f0 = g.var_edges[e0], f1 = g.var_edges[e0 + 1];
-                    const int f2 = d == 3 ? g.var_edges[e0 + 2] : f1;
                     const T n0 = nb[f0], n1 = nb[f1];
                     const T n2 = d == 3 ? nb[f2] : T(0);
                     lb = Lb[j] + (d == 3 ? T(0) + n0 + n1 + n2 : T(0) + n0 + n1);
@@ -423,10 +484,10 @@ __global__ void reduce_shots(const T *in, int B, int n, T scale, const T *upstre
 }
 
 template <typename T>
-size_t fwd_smem(const SoftGraph &g) { return sizeof(T) * ((size_t)g.E + g.N); }
+size_t fwd_smem(const SoftGraph &g) { return sizeof(T) * (size_t)soft_state_values(g); }
 template <typename T>
 size_t bwd_smem(const SoftGraph &g, int Tit) {
-    return sizeof(T) * (2 * (size_t)g.E + g.N + Tit);
+    return sizeof(T) * ((size_t)soft_state_values(g) + Tit);
 }
 
 template <typename T, int DCM>
@@ -448,8 +509,8 @@ cudaError_t run_forward_t(const SoftLaunch &L, cudaStream_t st) {
     a.shot_loss = static_cast<T *>(L.shot_loss);
     a.shot_gg = static_cast<T *>(L.shot_gg);
     a.shot_ga = static_cast<T *>(L.shot_ga);
-    a.shot_lb = static_cast<T *>(L.shot_lb);
     a.marg = static_cast<T *>(L.marg);
+    a.sst = soft_state_values(L.g);
     const size_t sm = fwd_smem<T>(L.g);
     cudaError_t e = cudaFuncSetAttribute(soft_forward<T, DCM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -482,7 +543,8 @@ cudaError_t run_backward_t(const SoftLaunch &L, cudaStream_t st) {
     a.shot_loss = static_cast<T *>(L.shot_loss);
     a.shot_gg = static_cast<T *>(L.shot_gg);
     a.shot_ga = static_cast<T *>(L.shot_ga);
-    a.shot_lb = static_cast<T *>(L.shot_lb);
+    a.shot_adj = static_cast<T *>(L.shot_adj);
+    a.sst = soft_state_values(L.g);
     const size_t sm = bwd_smem<T>(L.g, L.T_it);
     cudaError_t e = cudaFuncSetAttribute(soft_backward<T, DCM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -118,3 +118,34 @@ def test_first_leg_then_cluster_pipeline_matches_oracle():
     assert (st[todo] == sto).all() and (steps[todo] == stepso).all()
     assert (cor[todo] == Fo).all()
     assert (st[conv == 1] == QLDPC_CLUSTER_SKIPPED).all()
+
+
+def test_one_handle_with_skip_masks_of_growing_and_shrinking_batches():
+    """The handle's list of shots to post-process is allocated on the first masked call
+    and reallocated when a batch grows: masked calls of 30, 200, 70 and 12 shots on one
+    handle, one with every shot skipped and one with none, against the oracle."""
+    P = phenomenological_dem(BB72, 6, 0.04)
+    prm = ClusterParams(25, -0.5, 3.5, max_cluster_faults=512, max_clusters=4096)
+    dec = ClusterDecoder(P.row_ptr, P.col_idx, P.p, prm.bp_iters, prm.llr_accept, prm.llr_erase,
+                         prm.max_clusters, prm.max_cluster_faults)
+    try:
+        rng = np.random.default_rng(4)
+        for k, n in enumerate((30, 200, 70, 12, 12)):
+            F, sig = _shots(P, n, 50 + k)
+            skip = rng.random(n) < 0.5
+            if k == 3:
+                skip[:] = True
+            if k == 4:
+                skip[:] = False
+            syn = torch.from_numpy(pack_bits(sig).view(np.int64)).cuda()
+            cor = torch.zeros((n, dec.correction_words), dtype=torch.int64, device="cuda")
+            st, steps = dec.decode(syn, cor, skip=torch.from_numpy(skip.astype(np.uint8)).cuda())
+            torch.cuda.synchronize()
+            st, steps = st.cpu().numpy(), steps.cpu().numpy()
+            got = unpack_bits(cor.cpu().numpy().view(np.uint64), P.N)
+            assert (st[skip] == QLDPC_CLUSTER_SKIPPED).all() and (got[skip] == 0).all()
+            if (~skip).any():
+                ref = _oracle(P, sig[~skip], prm)
+                _assert_same((got[~skip], st[~skip], steps[~skip]), ref, f"call {k}")
+    finally:
+        dec.close()

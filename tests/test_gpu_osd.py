@@ -213,3 +213,34 @@ def test_osd_and_cluster_on_wider_check_families(dc_wide):
         assert st[b] == s_ and steps[b] == n, (b, st[b], s_, steps[b], n)
         if s_ == 1:
             assert (cor[b] == f).all()
+
+
+def test_one_handle_with_skip_masks_of_growing_and_shrinking_batches():
+    """The handle's list of shots to post-process is allocated on the first masked call
+    and reallocated when a batch grows: masked calls of 40, 300, 90 and 16 shots on one
+    handle, one with every shot skipped and one with none, against the oracle."""
+    P = phenomenological_dem(BB72, 6, 0.04)
+    prm = OSDParams(25, 4.0, 500)
+    osd = FilteredOSD(P.row_ptr, P.col_idx, P.p, prm.bp_iters, prm.llr_confident,
+                      prm.max_candidates)
+    try:
+        rng = np.random.default_rng(9)
+        for k, n in enumerate((40, 300, 90, 16, 16)):
+            F, sig = _shots(P, n, 30 + k)
+            skip = rng.random(n) < 0.5
+            if k == 3:
+                skip[:] = True
+            if k == 4:
+                skip[:] = False
+            syn = torch.from_numpy(pack_bits(sig).view(np.int64)).cuda()
+            cor = torch.zeros((n, osd.correction_words), dtype=torch.int64, device="cuda")
+            st, nc = osd.decode(syn, cor, skip=torch.from_numpy(skip.astype(np.uint8)).cuda())
+            torch.cuda.synchronize()
+            st, nc = st.cpu().numpy(), nc.cpu().numpy()
+            got = unpack_bits(cor.cpu().numpy().view(np.uint64), P.N)
+            assert (st[skip] == QLDPC_OSD_SKIPPED).all() and (nc[skip] == 0).all()
+            if (~skip).any():
+                ref = _oracle_osd(P, sig[~skip], prm)
+                _assert_same((got[~skip], st[~skip], nc[~skip]), ref, f"call {k}")
+    finally:
+        osd.close()

@@ -235,3 +235,52 @@ def test_fp32_padded_rows_with_empty_and_short_checks():
     assert np.abs(gg.cpu().numpy() - gg_ref).max() <= 1e-3 * np.abs(gg_ref).max()
     assert np.abs(ga.cpu().numpy() - ga_ref).max() <= 1e-3 * np.abs(ga_ref).max()
     soft.close()
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_odd_state_size_generic_fault_degrees_and_partial_last_segment(dtype):
+    """A 73-fault graph (the 72-qubit code-capacity matrix without its first column, plus
+    a fault of degree 1 and one of degree 4): a state of E + N values that is not a
+    multiple of 4, faults outside the degree-2/3 fast paths, and 23 iterations in
+    checkpoint segments of 5 (the last one of 3), against the oracle.  The adjoint leaves
+    the forward's checkpoints as they were (a second backward on the same workspace gives
+    the same gradients, bit for bit), and a workspace that does not start on a 16-byte
+    boundary is refused."""
+    P, F0, s0, gam0, alpha = _case(seed=6, B=16, T=23)
+    H = P.H[:, 1:].astype(np.uint8)
+    extra = np.zeros((H.shape[0], 2), np.uint8)
+    extra[4, 0] = 1
+    extra[:4, 1] = 1
+    H = np.concatenate([H, extra], axis=1)
+    N = H.shape[1]
+    rp = np.concatenate([[0], np.cumsum(H.sum(1))]).astype(np.int32)
+    ci = np.concatenate([np.nonzero(r)[0] for r in H]).astype(np.int32)
+    assert (N + 8 * H.shape[0]) % 4 != 0 and H.sum(1).max() <= 8
+    pr = np.concatenate([P.p[1:], [0.05, 0.05]])
+    F = sample_faults(pr, 6, 16)
+    s = syndromes_of(rp, ci, F)
+    gam = np.random.default_rng(6).uniform(0.0, 0.3, N)
+    tdt = getattr(torch, dtype)
+    if dtype == "float32":
+        gam = gam.astype(np.float32).astype(np.float64)
+        alpha = alpha.astype(np.float32).astype(np.float64)
+    L_ref, gg_ref, ga_ref, m_ref = soft_dmem(rp, ci, pr, gam, alpha, s, F,
+                                             eps=EPS32 if dtype == "float32" else 1e-15,
+                                             marginals=True)
+    soft = SoftDMem(rp, ci, pr, iterations=23, checkpoint_every=5, dtype=tdt)
+    syn, flt, g, a = _dev(None, F, s, gam, alpha, tdt)
+    loss, marg, ws = soft.forward(syn, flt, g, a, marginals=True)
+    gg, ga = soft.backward(syn, flt, g, a, ws)
+    gg2, ga2 = soft.backward(syn, flt, g, a, ws)
+    torch.cuda.synchronize()
+    tol_m, tol_g = (1e-4, 1e-3) if dtype == "float32" else (1e-11, 1e-9)
+    err = np.abs(marg.cpu().numpy() - m_ref) / np.maximum(1.0, np.abs(m_ref))
+    assert err.max() <= tol_m, err.max()
+    assert abs(loss.item() - L_ref) <= tol_m * L_ref
+    assert np.abs(gg.cpu().numpy() - gg_ref).max() <= tol_g * np.abs(gg_ref).max()
+    assert np.abs(ga.cpu().numpy() - ga_ref).max() <= tol_g * np.abs(ga_ref).max()
+    assert torch.equal(gg, gg2) and torch.equal(ga, ga2)
+    big = torch.empty(ws.numel() + 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(Exception, match="16-byte aligned"):
+        soft.forward(syn, flt, g, a, workspace=big[8:])
+    soft.close()
