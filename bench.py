@@ -693,20 +693,23 @@ def mixed_batch_variant(args, dev, stream, flush):
 
 # Special-function (MUFU) operations per edge per iteration of the float32 soft kernels:
 # forward tanh(nu/2) = 1 - 2/(1 + e^nu) (exponential, reciprocal) and
-# atanh(P) = log((1+P)/(1-P))/2 (reciprocal, logarithm); per reverse step the adjoint
-# evaluates tanh (2), atanh (2) and one reciprocal for 1/(1 - P^2), and it recomputes
-# the forward (4) of every iteration but the last of each checkpoint segment other than
-# the final one.
+# atanh(P) = log((1+P)/(1-P))/2 (reciprocal, logarithm).  The adjoint's recompute stores
+# each iteration's tanh(nu/2) rows, so a reverse step evaluates only atanh (2) and one
+# reciprocal for 1/(1 - P^2); the recompute runs the forward (4) of every iteration but
+# the last of each checkpoint segment other than the final one, and for those the tanh
+# rows alone (2).
 SOFT_XU_OPS_FORWARD = 4
-SOFT_XU_OPS_REVERSE = 5
+SOFT_XU_OPS_REVERSE = 3
+SOFT_XU_OPS_TANH = 2
 
 
 def soft_backward_ops_per_edge_iter(T, K):
     """Special-function operations per edge per iteration of the adjoint, averaged over
-    the T iterations (checkpoints every K): 5 T reverse plus 4 (T - ceil(T/K) + 1)
-    recomputed."""
+    the T iterations (checkpoints every K): 3 T reverse, 4 (T - ceil(T/K) + 1) recomputed
+    iterations and 2 (ceil(T/K) - 1) tanh passes."""
     nck = (T + K - 1) // K
-    return (SOFT_XU_OPS_REVERSE * T + SOFT_XU_OPS_FORWARD * (T - nck + 1)) / T
+    return (SOFT_XU_OPS_REVERSE * T + SOFT_XU_OPS_FORWARD * (T - nck + 1)
+            + SOFT_XU_OPS_TANH * (nck - 1)) / T
 
 
 def soft_roofline(edge_iters, ms, ops_per_edge_iter, sms):

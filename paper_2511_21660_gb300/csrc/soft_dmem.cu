@@ -174,14 +174,19 @@ __device__ __forceinline__ void fault_slots(const SoftGraph &g, int j, int &d, i
     }
 }
 
-// Check products of one row: P_k = prod_{l != k} tanh(nu_l/2), clamped.  The row
-// has d <= DCM edges (values v).  float32 forms them from prefix and suffix products
-// (O(d)); FP64 multiplies in increasing l, as the oracle does.
+// tau_k = tanh(nu_k/2) of one row of d <= DCM edges (values v); 1 on slots k >= d.
 template <typename T, int DCM>
-__device__ __forceinline__ void row_products(const T (&v)[DCM], int d, T eps, T (&tau)[DCM],
-                                             T (&P)[DCM], bool (&cl)[DCM]) {
+__device__ __forceinline__ void row_tanh(const T (&v)[DCM], int d, T (&tau)[DCM]) {
 #pragma unroll
     for (int k = 0; k < DCM; ++k) tau[k] = k < d ? RM<T>::tanh_half(v[k]) : T(1);
+}
+
+// Check products of one row: P_k = prod_{l != k} tau_l, clamped (cl_k: it was).  The
+// row has d <= DCM edges and tau = 1 on slots k >= d.  float32 forms them from prefix
+// and suffix products (O(d)); FP64 multiplies in increasing l, as the oracle does.
+template <typename T, int DCM>
+__device__ __forceinline__ void row_products(const T (&tau)[DCM], int d, T eps, T (&P)[DCM],
+                                             bool (&cl)[DCM]) {
     T suf[DCM];
     if constexpr (sizeof(T) == 4) {
         suf[DCM - 1] = T(1);
@@ -213,10 +218,12 @@ __device__ __forceinline__ void row_products(const T (&v)[DCM], int d, T eps, T 
     }
 }
 
-// One forward iteration t (1-based) on the shared state nu[E], Lam[N] (in place).
+// One forward iteration t (1-based) on the shared state nu[E], Lam[N] (in place).  With
+// tau_out, the check pass also stores each row's tanh(nu(t-1)/2) there (the adjoint's
+// saved state; padded rows whole, with 1 on the padding slots).
 template <typename T, int DCM>
 __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint64_t *sy, int t,
-                                               T *nu, T *Lam) {
+                                               T *nu, T *Lam, T *tau_out = nullptr) {
     const SoftGraph &g = a.g;
     const T at = a.alpha[t - 1];
     for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
@@ -225,7 +232,9 @@ __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint6
         T v[DCM], tau[DCM], P[DCM];
         bool cl[DCM];
         load_row<T, DCM>(nu + e0, i, d, v);
-        row_products<T, DCM>(v, d, a.eps, tau, P, cl);
+        row_tanh<T, DCM>(v, d, tau);
+        if (tau_out) store_row<T, DCM>(tau_out + e0, i, d, tau);
+        row_products<T, DCM>(tau, d, a.eps, P, cl);
         const T s = bit_of(sy, i) ? T(-2) : T(2);
 #pragma unroll
         for (int k = 0; k < DCM; ++k) v[k] = k < d ? at * s * RM<T>::atanh_(P[k]) : T(0);
@@ -265,6 +274,19 @@ __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint6
         }
     }
     __syncthreads();
+}
+
+// tanh(nu/2) of every row of the shared nu, stored to tau_out as in soft_iteration.
+template <typename T, int DCM>
+__device__ __forceinline__ void tau_pass(const SoftGraph &g, const T *nu, T *tau_out) {
+    for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
+        int e0, d;
+        row_span(g, i, e0, d);
+        T v[DCM], tau[DCM];
+        load_row<T, DCM>(nu + e0, i, d, v);
+        row_tanh<T, DCM>(v, d, tau);
+        store_row<T, DCM>(tau_out + e0, i, d, tau);
+    }
 }
 
 template <typename T>
@@ -330,7 +352,9 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_forward(SoftArgs<T> a) {
 // Adjoint.  Shared memory holds a.sst + T values, as much as the forward's state, so
 // the adjoint runs as many blocks per SM as the forward:
 //   * the recompute of a segment runs the forward iterations on nu[E], Lam[N] and
-//     stores the state before each of the segment's iterations in the segment buffer;
+//     stores, for each of the segment's iterations, what its reverse step needs of the
+//     state before it in the segment buffer: tanh(nu/2) of every row (written by the
+//     check pass that computes it) and Lambda;
 //   * the reverse steps keep nb[E] (adjoint of nu(t), then of mu(t)) in nu's place and
 //     Lb[N] (adjoint of Lambda) in Lam's place, and read the saved states from the
 //     segment buffer (the next step's state is prefetched into L2 by one bulk prefetch);
@@ -369,26 +393,32 @@ __global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD
         }
         copy_state(ck, nu, (int)S);  // nu, then Lam = nu + E
         __syncthreads();
-        // the states before iterations t0+1 .. t1 go to the segment buffer; iteration t1
-        // itself runs only in the last segment, whose Lambda(T) seeds the adjoint
+        // the saved states before iterations t0+1 .. t1 (tanh rows, then Lambda); iteration
+        // t1 itself runs only in the last segment, whose Lambda(T) seeds the adjoint (in the
+        // others only its tanh rows are formed).  Lam[j] is copied and later updated by the
+        // thread that owns j, so the copy needs no barrier.
         for (int t = t0 + 1; t <= t1; ++t) {
-            copy_state(nu, segb + (size_t)(t - t0 - 1) * S, (int)S);
-            __syncthreads();  // copied before the check pass overwrites nu
-            if (t < t1 || last) soft_iteration<T, DCM>(a, sy, t, nu, Lam);
+            T *st = segb + (size_t)(t - t0 - 1) * S;
+            for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) st[g.E + j] = Lam[j];
+            if (t < t1 || last)
+                soft_iteration<T, DCM>(a, sy, t, nu, Lam, st);
+            else
+                tau_pass<T, DCM>(g, nu, st);
         }
         if (last) {  // Lambda(T) is in Lam: Lb = adjoint of the loss sum, in place; nb = 0
             for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS)
                 Lb[j] = RM<T>::sigmoid(Lam[j]) - (bit_of(fy, j) ? T(0) : T(1));
             for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nb[e] = 0;
         } else {
+            __syncthreads();  // the tanh pass has read nu
             copy_state(adj, nu, (int)S);
         }
         __syncthreads();
         for (int t = t1; t > t0; --t) {
-            // the state before iteration t, from the segment buffer
-            const T *nu_prev = segb + (size_t)(t - t0 - 1) * S;
-            const T *L_prev = nu_prev + g.E;
-            if (threadIdx.x == 0 && t > t0 + 1) prefetch_l2(nu_prev - S, S * sizeof(T));
+            // the saved state before iteration t, from the segment buffer
+            const T *tau_prev = segb + (size_t)(t - t0 - 1) * S;
+            const T *L_prev = tau_prev + g.E;
+            if (threadIdx.x == 0 && t > t0 + 1) prefetch_l2(tau_prev - S, S * sizeof(T));
             const bool inner = t - 1 >= 1;
             // fault adjoint: lambda_bar = Lb + sum nb;  mu_bar_e = lambda_bar - nb_e
             for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
@@ -421,10 +451,15 @@ __global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD
             for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
                 int e0, d;
                 row_span(g, i, e0, d);
-                T v[DCM], tau[DCM], P[DCM], Pb[DCM], mbv[DCM];
+                T tau[DCM], P[DCM], Pb[DCM], mbv[DCM];
                 bool cl[DCM];
-                load_row<T, DCM>(nu_prev + e0, i, d, v);
-                row_products<T, DCM>(v, d, a.eps, tau, P, cl);
+                load_row<T, DCM>(tau_prev + e0, i, d, tau);
+                if constexpr (!padded_rows<T, DCM>()) {  // slots k >= d were read as 0
+#pragma unroll
+                    for (int k = 0; k < DCM; ++k)
+                        if (k >= d) tau[k] = T(1);
+                }
+                row_products<T, DCM>(tau, d, a.eps, P, cl);
                 load_row<T, DCM>(nb + e0, i, d, mbv);
                 const T s2 = bit_of(sy, i) ? T(-2) : T(2);
 #pragma unroll

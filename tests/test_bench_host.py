@@ -151,13 +151,14 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
 def test_soft_roofline_counts_special_function_operations():
     """4 (forward) special-function operations per edge-iteration against 32 results per
     clock per SM: batch 4096, E = 7344, 25 iterations in 2.78 ms.  The adjoint with
-    checkpoints every 5 iterations: 5 per reverse step plus 4 for each of the 21
-    recomputed iterations (25 less the last of the first four segments)."""
+    checkpoints every 5 iterations: 3 per reverse step (the recompute keeps the tanh
+    values), 4 for each of the 21 recomputed iterations (25 less the last of the first
+    four segments) and 2 for the tanh rows of each of those four last iterations."""
     ei = 7344 * 25 * 4096
     r = bench.soft_roofline(ei, 2.78, bench.SOFT_XU_OPS_FORWARD, 152)
     peak = 32 * 152 * bench.sm_max_mhz() * 1e6
     assert r["bound"] == "xu" and r["peak"] == pytest.approx(peak / 1e12)
     assert r["frac"] == pytest.approx(4 * ei / 2.78e-3 / peak)
-    assert bench.soft_backward_ops_per_edge_iter(25, 5) == pytest.approx((5 * 25 + 4 * 21) / 25)
-    assert bench.soft_backward_ops_per_edge_iter(25, 25) == pytest.approx(9)
-    assert bench.soft_backward_ops_per_edge_iter(25, 1) == pytest.approx(5 + 4 / 25)
+    assert bench.soft_backward_ops_per_edge_iter(25, 5) == pytest.approx((3 * 25 + 4 * 21 + 2 * 4) / 25)
+    assert bench.soft_backward_ops_per_edge_iter(25, 25) == pytest.approx(7)
+    assert bench.soft_backward_ops_per_edge_iter(25, 1) == pytest.approx(3 + 4 / 25 + 2 * 24 / 25)
