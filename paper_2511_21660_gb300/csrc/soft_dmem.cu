@@ -23,9 +23,16 @@
 namespace qldpc {
 namespace {
 
-constexpr int SOFT_THREADS = 256;
+// Threads per block of the forward and of the adjoint, and the adjoint's resident blocks
+// per SM (float32 rows of up to 8 edges; its register budget follows from them).
+#ifndef SOFT_FWD_THREADS
+#define SOFT_FWD_THREADS 512
+#endif
+#ifndef SOFT_BWD_THREADS
+#define SOFT_BWD_THREADS 384
+#endif
 #ifndef SOFT_BWD_MINB
-#define SOFT_BWD_MINB 5
+#define SOFT_BWD_MINB 4
 #endif
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -89,14 +96,14 @@ __device__ __forceinline__ uint32_t bit_of(const uint64_t *v, int i) {
 
 // Sum of one value per thread in a fixed order (warp shuffles, then warp 0):
 // deterministic.  Every thread must call it; thread 0 gets the total.
-template <typename T>
+template <int NT, typename T>
 __device__ __forceinline__ T block_sum(T v, T *red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     T s = 0;
     if (threadIdx.x == 0)
-        for (int q = 0; q < SOFT_THREADS / 32; ++q) s += red[q];
+        for (int q = 0; q < NT / 32; ++q) s += red[q];
     __syncthreads();
     return s;
 }
@@ -221,12 +228,12 @@ __device__ __forceinline__ void row_products(const T (&tau)[DCM], int d, T eps, 
 // One forward iteration t (1-based) on the shared state nu[E], Lam[N] (in place).  With
 // tau_out, the check pass also stores each row's tanh(nu(t-1)/2) there (the adjoint's
 // saved state; padded rows whole, with 1 on the padding slots).
-template <typename T, int DCM>
+template <int NT, typename T, int DCM>
 __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint64_t *sy, int t,
                                                T *nu, T *Lam, T *tau_out = nullptr) {
     const SoftGraph &g = a.g;
     const T at = a.alpha[t - 1];
-    for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
+    for (int i = threadIdx.x; i < g.M; i += NT) {
         int e0, d;
         row_span(g, i, e0, d);
         T v[DCM], tau[DCM], P[DCM];
@@ -241,7 +248,7 @@ __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint6
         store_row<T, DCM>(nu + e0, i, d, v);
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
+    for (int j = threadIdx.x; j < g.N; j += NT) {
         int d, b, e0, e1, e2;
         fault_slots(g, j, d, b, e0, e1, e2);
         const T lam = (T(1) - a.gamma[j]) * a.w[j] + a.gamma[j] * Lam[j];
@@ -277,9 +284,9 @@ __device__ __forceinline__ void soft_iteration(const SoftArgs<T> &a, const uint6
 }
 
 // tanh(nu/2) of every row of the shared nu, stored to tau_out as in soft_iteration.
-template <typename T, int DCM>
+template <int NT, typename T, int DCM>
 __device__ __forceinline__ void tau_pass(const SoftGraph &g, const T *nu, T *tau_out) {
-    for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
+    for (int i = threadIdx.x; i < g.M; i += NT) {
         int e0, d;
         row_span(g, i, e0, d);
         T v[DCM], tau[DCM];
@@ -289,11 +296,11 @@ __device__ __forceinline__ void tau_pass(const SoftGraph &g, const T *nu, T *tau
     }
 }
 
-template <typename T>
+template <int NT, typename T>
 __device__ __forceinline__ void init_state(const SoftArgs<T> &a, T *nu, T *Lam) {
     const SoftGraph &g = a.g;
-    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) Lam[j] = a.w[j];
-    for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nu[e] = a.w[g.col_idx[e]];
+    for (int j = threadIdx.x; j < g.N; j += NT) Lam[j] = a.w[j];
+    for (int e = threadIdx.x; e < g.E; e += NT) nu[e] = a.w[g.col_idx[e]];
     __syncthreads();
 }
 
@@ -307,45 +314,46 @@ __device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
 // adjoint alone).  float32 moves 16-byte vectors: every state starts on a 16-byte
 // boundary (the stride a.sst is a multiple of 4 values, the workspace is 16-byte
 // aligned) and n is a multiple of 4.
-template <typename T>
+template <int NT, typename T>
 __device__ __forceinline__ void copy_state(const T *src, T *dst, int n) {
     if constexpr (sizeof(T) == 4) {
         const float4 *s4 = reinterpret_cast<const float4 *>(src);
         float4 *d4 = reinterpret_cast<float4 *>(dst);
 #pragma unroll 4
-        for (int q = threadIdx.x; q < n / 4; q += SOFT_THREADS) d4[q] = s4[q];
+        for (int q = threadIdx.x; q < n / 4; q += NT) d4[q] = s4[q];
     } else {
-        for (int e = threadIdx.x; e < n; e += SOFT_THREADS) dst[e] = src[e];
+        for (int e = threadIdx.x; e < n; e += NT) dst[e] = src[e];
     }
 }
 
 // Forward.  Shared memory: nu[E], Lam[N] (a.sst values).  The state before iterations
 // 1, K + 1, 2K + 1, ... is stored as a checkpoint.
 template <typename T, int DCM>
-__global__ void __launch_bounds__(SOFT_THREADS) soft_forward(SoftArgs<T> a) {
+__global__ void __launch_bounds__(SOFT_FWD_THREADS) soft_forward(SoftArgs<T> a) {
+    constexpr int NT = SOFT_FWD_THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SoftGraph &g = a.g;
     T *nu = reinterpret_cast<T *>(smem_raw);
     T *Lam = nu + g.E;
-    __shared__ T red[SOFT_THREADS / 32];
+    __shared__ T red[NT / 32];
     const int b = blockIdx.x;
     const uint64_t *sy = a.syn + (size_t)b * g.syn_words;
     const uint64_t *fy = a.faults + (size_t)b * g.cor_words;
     const size_t S = (size_t)a.sst;
-    init_state(a, nu, Lam);
+    init_state<NT>(a, nu, Lam);
     for (int t = 1; t <= a.T_it; ++t) {
         if ((t - 1) % a.K == 0) {
-            copy_state(nu, a.ckpt + ((size_t)b * a.nck + (t - 1) / a.K) * S, (int)S);
+            copy_state<NT>(nu, a.ckpt + ((size_t)b * a.nck + (t - 1) / a.K) * S, (int)S);
             __syncthreads();  // copied before the check pass overwrites nu
         }
-        soft_iteration<T, DCM>(a, sy, t, nu, Lam);
+        soft_iteration<NT, T, DCM>(a, sy, t, nu, Lam);
     }
     T part = 0;
-    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
+    for (int j = threadIdx.x; j < g.N; j += NT) {
         part += bit_of(fy, j) ? RM<T>::softplus(Lam[j]) : RM<T>::softplus(-Lam[j]);
         if (a.marg) a.marg[(size_t)b * g.N + j] = Lam[j];
     }
-    const T tot = block_sum(part, red);
+    const T tot = block_sum<NT>(part, red);
     if (threadIdx.x == 0) a.shot_loss[b] = tot;
 }
 
@@ -363,8 +371,9 @@ __global__ void __launch_bounds__(SOFT_THREADS) soft_forward(SoftArgs<T> a) {
 // The gamma gradient of fault j is touched only by the thread that owns j, so it stays
 // in global memory (shot_gg: coalesced, cached).
 template <typename T, int DCM>
-__global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD_MINB : 1)
+__global__ void __launch_bounds__(SOFT_BWD_THREADS, padded_rows<T, DCM>() ? SOFT_BWD_MINB : 1)
     soft_backward(SoftArgs<T> a) {
+    constexpr int NT = SOFT_BWD_THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SoftGraph &g = a.g;
     T *nu = reinterpret_cast<T *>(smem_raw);
@@ -372,7 +381,7 @@ __global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD
     T *nb = nu;
     T *Lb = Lam;
     T *as = nu + a.sst;
-    __shared__ T red[SOFT_THREADS / 32];
+    __shared__ T red[NT / 32];
     const int b = blockIdx.x;
     T *gs = a.shot_gg + (size_t)b * g.N;
     const uint64_t *sy = a.syn + (size_t)b * g.syn_words;
@@ -380,18 +389,18 @@ __global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD
     const size_t S = (size_t)a.sst;
     T *segb = a.seg + (size_t)b * a.K * S;
     T *adj = a.shot_adj + (size_t)b * S;
-    for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) gs[j] = 0;
-    for (int t = threadIdx.x; t < a.T_it; t += SOFT_THREADS) as[t] = 0;
+    for (int j = threadIdx.x; j < g.N; j += NT) gs[j] = 0;
+    for (int t = threadIdx.x; t < a.T_it; t += NT) as[t] = 0;
 
     for (int s = a.nck - 1; s >= 0; --s) {
         const int t0 = s * a.K, t1 = min(a.T_it, t0 + a.K);
         const bool last = s == a.nck - 1;
         T *ck = a.ckpt + ((size_t)b * a.nck + s) * S;
         if (!last) {  // nb and Lb of the segment after this one wait in global scratch
-            copy_state(nu, adj, (int)S);
+            copy_state<NT>(nu, adj, (int)S);
             __syncthreads();
         }
-        copy_state(ck, nu, (int)S);  // nu, then Lam = nu + E
+        copy_state<NT>(ck, nu, (int)S);  // nu, then Lam = nu + E
         __syncthreads();
         // the saved states before iterations t0+1 .. t1 (tanh rows, then Lambda); iteration
         // t1 itself runs only in the last segment, whose Lambda(T) seeds the adjoint (in the
@@ -399,19 +408,19 @@ __global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD
         // thread that owns j, so the copy needs no barrier.
         for (int t = t0 + 1; t <= t1; ++t) {
             T *st = segb + (size_t)(t - t0 - 1) * S;
-            for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) st[g.E + j] = Lam[j];
+            for (int j = threadIdx.x; j < g.N; j += NT) st[g.E + j] = Lam[j];
             if (t < t1 || last)
-                soft_iteration<T, DCM>(a, sy, t, nu, Lam, st);
+                soft_iteration<NT, T, DCM>(a, sy, t, nu, Lam, st);
             else
-                tau_pass<T, DCM>(g, nu, st);
+                tau_pass<NT, T, DCM>(g, nu, st);
         }
         if (last) {  // Lambda(T) is in Lam: Lb = adjoint of the loss sum, in place; nb = 0
-            for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS)
+            for (int j = threadIdx.x; j < g.N; j += NT)
                 Lb[j] = RM<T>::sigmoid(Lam[j]) - (bit_of(fy, j) ? T(0) : T(1));
-            for (int e = threadIdx.x; e < g.E; e += SOFT_THREADS) nb[e] = 0;
+            for (int e = threadIdx.x; e < g.E; e += NT) nb[e] = 0;
         } else {
             __syncthreads();  // the tanh pass has read nu
-            copy_state(adj, nu, (int)S);
+            copy_state<NT>(adj, nu, (int)S);
         }
         __syncthreads();
         for (int t = t1; t > t0; --t) {
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD
             if (threadIdx.x == 0 && t > t0 + 1) prefetch_l2(tau_prev - S, S * sizeof(T));
             const bool inner = t - 1 >= 1;
             // fault adjoint: lambda_bar = Lb + sum nb;  mu_bar_e = lambda_bar - nb_e
-            for (int j = threadIdx.x; j < g.N; j += SOFT_THREADS) {
+            for (int j = threadIdx.x; j < g.N; j += NT) {
                 int d, e0, f0, f1, f2;
                 fault_slots(g, j, d, e0, f0, f1, f2);
                 T lb;
@@ -448,7 +457,7 @@ __global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD
             // check adjoint: mu_e = alpha_t s 2 atanh(P_e)
             const T at = a.alpha[t - 1];
             T apart = 0;
-            for (int i = threadIdx.x; i < g.M; i += SOFT_THREADS) {
+            for (int i = threadIdx.x; i < g.M; i += NT) {
                 int e0, d;
                 row_span(g, i, e0, d);
                 T tau[DCM], P[DCM], Pb[DCM], mbv[DCM];
@@ -500,12 +509,12 @@ __global__ void __launch_bounds__(SOFT_THREADS, padded_rows<T, DCM>() ? SOFT_BWD
                 }
                 store_row<T, DCM>(nb + e0, i, d, mbv);
             }
-            const T asum = block_sum(apart, red);  // includes the barrier
+            const T asum = block_sum<NT>(apart, red);  // includes the barrier
             if (threadIdx.x == 0) as[t - 1] += asum;
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < a.T_it; t += SOFT_THREADS) a.shot_ga[(size_t)b * a.T_it + t] = as[t];
+    for (int t = threadIdx.x; t < a.T_it; t += NT) a.shot_ga[(size_t)b * a.T_it + t] = as[t];
 }
 
 // out[c] = scale * upstream * sum_b in[b][c], summed over b in order.
@@ -550,7 +559,7 @@ cudaError_t run_forward_t(const SoftLaunch &L, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(soft_forward<T, DCM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    soft_forward<T, DCM><<<L.B, SOFT_THREADS, sm, st>>>(a);
+    soft_forward<T, DCM><<<L.B, SOFT_FWD_THREADS, sm, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const T scale = T(1) / ((T)L.B * (T)L.g.N);
@@ -584,7 +593,7 @@ cudaError_t run_backward_t(const SoftLaunch &L, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(soft_backward<T, DCM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    soft_backward<T, DCM><<<L.B, SOFT_THREADS, sm, st>>>(a);
+    soft_backward<T, DCM><<<L.B, SOFT_BWD_THREADS, sm, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const T scale = T(1) / ((T)L.B * (T)L.g.N);
