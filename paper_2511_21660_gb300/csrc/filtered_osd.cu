@@ -22,7 +22,7 @@
 // A row is a bitset over ranking positions, 32 columns per word.
 #include "gf2_warp.cuh"
 #include "post_internal.h"
-#include "relay_device.cuh"
+#include "post_bp.cuh"
 
 namespace qldpc {
 namespace {
@@ -53,11 +53,11 @@ __device__ __forceinline__ void bitonic_sort(uint64_t *keys, int n) {
     }
 }
 
-// Several blocks per SM where the kernel fits in 64 registers without spilling (256
-// threads x 12 faults: 4 blocks; 512 x 8 with rows of up to 16 slots: 2): the single-warp
-// stages and barriers of one shot then overlap the other blocks' work.
+// Several blocks per SM (256 threads x 12 faults: 5 blocks in 48 registers, the plain BP
+// holding only Lambda_j and w_j per fault; 512 x 8 with rows of up to 16 slots: 2 in 64):
+// the single-warp stages and barriers of one shot then overlap the other blocks' work.
 template <int NT, int VPT, int DC, int DV>
-__global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 : 1)) osd_decode(FusedGraph g, DevParams p, OsdArgs o,
+__global__ void __launch_bounds__(NT, NT == 256 ? 5 : (VPT <= 8 && DC <= 16 ? 2 : 1)) osd_decode(FusedGraph g, DevParams p, OsdArgs o,
                                                     const uint64_t *__restrict__ syn,
                                                     const int32_t *__restrict__ list, int B,
                                                     OsdOut out, unsigned int *counter) {
@@ -72,7 +72,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
     uint32_t *fb = fw + g.f_words;
     uint32_t *sg = fb + g.f_words;
     uint32_t *par = sg + 2 * g.syn_words;
-    float *ws = reinterpret_cast<float *>(par + 2 * g.m_words);
     __shared__ int s_shot, s_cnt, s_bad, s_rows;
     // the shots: list[0 .. counter[1]) (the host's compaction of a skip mask), else 0 .. B-1
     const int n_work = list ? (int)counter[1] : B;
@@ -81,9 +80,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
 
     for (;;) {
         // per-shot registers, declared here so that nothing of them lives across shots
-        float Lam[VPT], bb[VPT], gg[VPT];
+        float Lam[VPT];
 #pragma unroll
-        for (int r = 0; r < VPT; ++r) Lam[r] = bb[r] = gg[r] = 0.0f;
+        for (int r = 0; r < VPT; ++r) Lam[r] = 0.0f;
         __syncthreads();  // the previous shot is done with shared memory
         if (tid == 0) s_shot = (int)atomicAdd(counter, 1u);
         __syncthreads();
@@ -96,8 +95,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : (VPT <= 8 && DC <= 16 ? 2 
             s_bad = 0;
             s_rows = 0;
         }
-        plain_bp<NT, VPT, DC, DV>(g, p, o.bp_iters, syn + (size_t)shot * g.syn_words, msg, fw,
-                                  sg, par, ws, Lam, bb, gg);
+        plain_bp_marginals<NT, VPT, DC, DV>(g, p.clip, o.bp_iters, syn + (size_t)shot * g.syn_words,
+                                            msg, sg, par, Lam);
 
         // 2. ranking: candidates Lambda_j < llr_conf, keys (Lambda_j, j)
 #pragma unroll

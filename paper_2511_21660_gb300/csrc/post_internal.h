@@ -54,7 +54,7 @@ __host__ __device__ inline size_t osd_union_bytes(const FusedGraph &g, const Osd
 }
 inline size_t osd_smem_bytes(const FusedGraph &g, const OsdArgs &o) {
     return osd_union_bytes(g, o) + 8 * (size_t)g.f_words + 8 * (size_t)g.syn_words +
-           8 * (size_t)g.m_words + 4 * (size_t)g.N + 64;
+           8 * (size_t)g.m_words + 64;
 }
 
 // Cluster decoder (paper Sec. 2.5 and Sec. 6) after plain BP: partial correction,
