@@ -13,11 +13,12 @@
 // One block per shot.  The forward keeps nu (edge order of the CSR) and Lambda in
 // shared memory and stores them every K iterations (checkpoints).  The adjoint
 // walks the checkpoint segments backwards: it recomputes the segment's forward from
-// its checkpoint, keeping each iteration's nu(t-1), Lambda(t-1) in a global
-// segment buffer, then runs the reverse iterations.  Only the last segment runs its
-// final iteration again (for Lambda(T)); in the others the recompute stops one
-// iteration short, and the state it ends on is the first reverse step's input.  Per-shot gradients are summed
-// over shots in a fixed order, so results are deterministic.
+// its checkpoint, keeping what each reverse step needs of the state before iteration
+// t (the rows' tanh(nu(t-1)/2) and Lambda(t-1)) in a global segment buffer, then runs
+// the reverse iterations.  Only the last segment runs its final iteration again (for
+// Lambda(T)); in the others the recompute forms only the tanh rows of that iteration's
+// input.  Per-shot gradients are summed over shots in a fixed order, so results are
+// deterministic.
 #include "soft_internal.h"
 
 namespace qldpc {
