@@ -46,6 +46,18 @@ __device__ __forceinline__ void st_half_sat(unsigned char *base, int off, float 
     *reinterpret_cast<unsigned short *>(base + off) = h;
 }
 
+__device__ __forceinline__ unsigned short ld_half_bits(const unsigned char *base, int off) {
+    return *reinterpret_cast<const unsigned short *>(base + off);
+}
+
+// x + h for a binary16 operand h in one float32 addition (the widening of h is exact,
+// so this is __fadd_rn(x, __half2float(h)) without a separate conversion).
+__device__ __forceinline__ float add_f16(float x, unsigned short h) {
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(h), "f"(x));
+    return d;
+}
+
 // x + 0 = x for x != 0 and -0 + 0 = +0.  Applied to lambda(0) and to
 // (1 - gamma) lambda(0) at the start of a leg, it guarantees that lambda(t) and
 // therefore every stored message nu (a sum starting from lambda(t)) is never -0,
@@ -130,9 +142,51 @@ __device__ __forceinline__ void leg_init(const FusedGraph &g, const DevParams &p
     }
 }
 
+// Two smallest of n values (with multiplicity) by a pairwise tree: sorted pairs, then
+// merges of sorted pairs, (l, h) = (min(l1, l2), min(max(l1, l2), min(h1, h2))).  min
+// and max are exact, so the result is the one a sequential scan gives, in log2(n)
+// dependent steps instead of n.  V is float or __half2 (two checks at once).
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ __half2 vmin(__half2 a, __half2 b) { return __hmin2(a, b); }
+__device__ __forceinline__ __half2 vmax(__half2 a, __half2 b) { return __hmax2(a, b); }
+
+// Rows wider than 8 slots keep the sequential scan (the tree's live values would spill).
+template <int n, typename V>
+__device__ __forceinline__ void two_smallest(const V (&a)[n], V &m1, V &m2) {
+    static_assert(n >= 2 && (n & (n - 1)) == 0, "power-of-two row capacity");
+    if constexpr (n > 8) {
+        m1 = vmin(a[0], a[1]);
+        m2 = vmax(a[0], a[1]);
+#pragma unroll
+        for (int k = 2; k < n; ++k) {
+            m2 = vmin(m2, vmax(m1, a[k]));
+            m1 = vmin(m1, a[k]);
+        }
+        return;
+    }
+    V lo[n / 2], hi[n / 2];
+#pragma unroll
+    for (int k = 0; k < n / 2; ++k) {
+        lo[k] = vmin(a[2 * k], a[2 * k + 1]);
+        hi[k] = vmax(a[2 * k], a[2 * k + 1]);
+    }
+#pragma unroll
+    for (int w = n / 2; w > 1; w >>= 1) {
+#pragma unroll
+        for (int k = 0; k < w / 2; ++k) {
+            const V l = vmin(lo[2 * k], lo[2 * k + 1]);
+            hi[k] = vmin(vmax(lo[2 * k], lo[2 * k + 1]), vmin(hi[2 * k], hi[2 * k + 1]));
+            lo[k] = l;
+        }
+    }
+    m1 = lo[0];
+    m2 = hi[0];
+}
+
 // Check pass, float32 messages: mu_{i->j}(t) from nu(t-1) for every check, in place.
-// (m1, m2) = the two smallest magnitudes of the check's slots (with multiplicity),
-// so the min over the excluded set of slot k is m2 if |nu_k| = m1, else m1.
+// (m1, m2) = the two smallest magnitudes of the check's slots (with multiplicity) and
+// of {C, C}, so the min over the excluded set of slot k is m2 if |nu_k| = m1, else m1.
 // Padding slots hold C, which is also the min over an empty set, and keep it.
 // The sign is (-1)^sigma_i times the product of all signs times sign(nu_k).
 // Slots are processed in physical order: the rule does not depend on the order.
@@ -157,15 +211,21 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, cons
             v[4 * k4 + 2] = t.z;
             v[4 * k4 + 3] = t.w;
         }
-        float m1 = C, m2 = C;
+        float a[DC], m1, m2;
+        uint32_t x[DC / 2];
 #pragma unroll
-        for (int k = 0; k < DC; ++k) {
-            const float a = fabsf(v[k]);
-            m2 = fminf(m2, fmaxf(m1, a));
-            m1 = fminf(m1, a);
-            sx ^= __float_as_uint(v[k]);
-        }
-        sx &= 0x80000000u;
+        for (int k = 0; k < DC; ++k) a[k] = fabsf(v[k]);
+        two_smallest<DC>(a, m1, m2);
+        m1 = fminf(m1, C);
+        m2 = fminf(m2, C);
+#pragma unroll
+        for (int k = 0; k < DC / 2; ++k)
+            x[k] = __float_as_uint(v[2 * k]) ^ __float_as_uint(v[2 * k + 1]);
+#pragma unroll
+        for (int w = DC / 2; w > 1; w >>= 1)
+#pragma unroll
+            for (int k = 0; k < w / 2; ++k) x[k] = x[2 * k] ^ x[2 * k + 1];
+        sx = (sx ^ x[0]) & 0x80000000u;
         // Slot k holds a smallest magnitude iff |nu_k| <= m1 (no |nu_k| is below m1);
         // its excluded minimum is then m2 (= m1 on a tie), else m1.  Both candidates
         // carry the sign of the whole product; one XOR takes the slot's own sign out.
@@ -173,7 +233,7 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, float *msg, cons
         float o[DC];
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
-            const uint32_t c = fabsf(v[k]) <= m1 ? s2 : s1;
+            const uint32_t c = a[k] <= m1 ? s2 : s1;
             o[k] = __uint_as_float(c ^ (__float_as_uint(v[k]) & 0x80000000u));
         }
         if (deg < DC) {  // v[k] is physical slot k ^ 4cs, logical slot k ^ 4cs ^ swz(i)
@@ -216,23 +276,27 @@ __device__ __forceinline__ void check_pass(const FusedGraph &g, __half *msg, con
             v[4 * k4 + 2] = t.z;
             v[4 * k4 + 3] = t.w;
         }
-        __half2 m1 = C2, m2 = C2;
+        __half2 a[DC], m1, m2;
+        uint32_t x[DC / 2];
 #pragma unroll
-        for (int k = 0; k < DC; ++k) {
-            const __half2 a = __habs2(*reinterpret_cast<const __half2 *>(&v[k]));
-            m2 = __hmin2(m2, __hmax2(m1, a));
-            m1 = __hmin2(m1, a);
-            sx ^= v[k];
-        }
-        sx &= 0x80008000u;
+        for (int k = 0; k < DC; ++k) a[k] = __habs2(*reinterpret_cast<const __half2 *>(&v[k]));
+        two_smallest<DC>(a, m1, m2);
+        m1 = __hmin2(m1, C2);
+        m2 = __hmin2(m2, C2);
+#pragma unroll
+        for (int k = 0; k < DC / 2; ++k) x[k] = v[2 * k] ^ v[2 * k + 1];
+#pragma unroll
+        for (int w = DC / 2; w > 1; w >>= 1)
+#pragma unroll
+            for (int k = 0; k < w / 2; ++k) x[k] = x[2 * k] ^ x[2 * k + 1];
+        sx = (sx ^ x[0]) & 0x80008000u;
         const uint32_t u1 = *reinterpret_cast<const uint32_t *>(&m1);
         const uint32_t u2 = *reinterpret_cast<const uint32_t *>(&m2);
         const uint32_t s1 = u1 | sx, s2 = u2 | sx;  // candidates with the product's sign
         uint32_t o[DC];
 #pragma unroll
         for (int k = 0; k < DC; ++k) {
-            const __half2 a = __habs2(*reinterpret_cast<const __half2 *>(&v[k]));
-            const uint32_t eq = __hle2_mask(a, m1);
+            const uint32_t eq = __hle2_mask(a[k], m1);
             o[k] = ((s2 & eq) | (s1 & ~eq)) ^ (v[k] & 0x80008000u);
         }
         if (!full) {
@@ -259,21 +323,22 @@ __device__ __forceinline__ float fault_update(unsigned char *msg, const int (&sl
                                               float lam, float C) {
     // binary16 storage with C = 65504 (its default): the saturating store clamps the
     // messages, so only the marginal needs an explicit clamp
+    // the binary16 operands enter the float32 sums through mixed-precision additions
     if constexpr (sizeof(MT) == 2) {
         if (C == 65504.0f && (deg == 3 || deg == 2)) {
-            const float mu0 = Msg<MT>::ld(msg, sl[0]), mu1 = Msg<MT>::ld(msg, sl[1]);
-            const float s0 = __fadd_rn(lam, mu0);
+            const unsigned short mu0 = ld_half_bits(msg, sl[0]), mu1 = ld_half_bits(msg, sl[1]);
+            const float s0 = add_f16(lam, mu0);
             if (deg == 3) {
-                const float mu2 = Msg<MT>::ld(msg, sl[2]);
-                const float s01 = __fadd_rn(s0, mu1);
-                st_half_sat(msg, sl[0], __fadd_rn(__fadd_rn(lam, mu1), mu2));
-                st_half_sat(msg, sl[1], __fadd_rn(s0, mu2));
+                const unsigned short mu2 = ld_half_bits(msg, sl[2]);
+                const float s01 = add_f16(s0, mu1);
+                st_half_sat(msg, sl[0], add_f16(add_f16(lam, mu1), mu2));
+                st_half_sat(msg, sl[1], add_f16(s0, mu2));
                 st_half_sat(msg, sl[2], s01);
-                return clampc(__fadd_rn(s01, mu2), C);
+                return clampc(add_f16(s01, mu2), C);
             }
-            st_half_sat(msg, sl[0], __fadd_rn(lam, mu1));
+            st_half_sat(msg, sl[0], add_f16(lam, mu1));
             st_half_sat(msg, sl[1], s0);
-            return clampc(__fadd_rn(s0, mu1), C);
+            return clampc(add_f16(s0, mu1), C);
         }
     }
     // The clamp is the identity unless some value exceeds C in magnitude, so it is
