@@ -342,8 +342,9 @@ __device__ __forceinline__ float fault_update(unsigned char *msg, const int (&sl
         }
     }
     // The clamp is the identity unless some value exceeds C in magnitude, so it is
-    // applied only then (same values either way).
-    if (deg == 3) {
+    // applied only then (same values either way).  Binary16 storage with another C takes
+    // the generic loop (less code in the persistent kernel; the same sums and clamps).
+    if (sizeof(MT) == 4 && deg == 3) {
         const float mu0 = Msg<MT>::ld(msg, sl[0]), mu1 = Msg<MT>::ld(msg, sl[1]),
                     mu2 = Msg<MT>::ld(msg, sl[2]);
         const float s0 = __fadd_rn(lam, mu0), s01 = __fadd_rn(s0, mu1);
@@ -360,7 +361,7 @@ __device__ __forceinline__ float fault_update(unsigned char *msg, const int (&sl
         Msg<MT>::st(msg, sl[2], n2);
         return L;
     }
-    if (deg == 2) {
+    if (sizeof(MT) == 4 && deg == 2) {
         const float mu0 = Msg<MT>::ld(msg, sl[0]), mu1 = Msg<MT>::ld(msg, sl[1]);
         const float s0 = __fadd_rn(lam, mu0);
         float n0 = __fadd_rn(lam, mu1), n1 = s0, L = __fadd_rn(s0, mu1);
